@@ -1,0 +1,227 @@
+/*
+ * dctgb.h - C ABI of the GB300 (sm_103a) Cordic-based Loeffler DCT image codec.
+ *
+ * The library implements the compression path of "CUDA based performance
+ * evaluation of the computational efficiency of the DCT image compression
+ * technique on both the CPU and GPU": a per-8x8-block Cordic-based Loeffler
+ * forward DCT (Sec. 2.5.2, Fig. 1), a quantiser, the inverse DCT (Sec. 3.2
+ * runs DCT, quantiser and IDCT as separate kernels) and the PSNR of the
+ * reconstruction (Sec. 4.1, Eq. 23 and Eq. 24).  Numeric choices the paper
+ * leaves open (fixed-point widths, CORDIC iteration count, rounding, table
+ * scaling, padding) are those of include/dctgb_spec.json; dct_spec_query()
+ * reports the values compiled into the library.
+ *
+ * Conventions shared by every entry point:
+ *  - All image, coefficient and result pointers are DEVICE pointers unless
+ *    the parameter name ends in _host.  The caller owns them; the library
+ *    never frees or keeps them past the call (dct_batch_prepare keeps them
+ *    until the next prepare or dct_plan_destroy, see there).
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).  No call synchronises unless
+ *    it writes a _host output that depends on GPU results (documented).
+ *  - Arguments are checked on the host before anything is enqueued; a bad
+ *    argument returns DCT_ERR_INVALID_ARG and enqueues nothing.  Launch
+ *    errors return DCT_ERR_CUDA.  Device code never traps or asserts.
+ *  - dct_last_error() returns a thread-local message for the last failure.
+ *  - Samples are uint8.  A plane is width x height samples with `pitch`
+ *    bytes between row starts (pitch >= width).  Planes whose width or
+ *    height is not a multiple of 8 are padded by edge replication inside the
+ *    transform; only real samples are written or counted.
+ *  - Coefficients are int16, block-major: plane p's block (by, bx) holds 64
+ *    values in natural order u*8+v (u vertical frequency, v horizontal) at
+ *    element offset coeff_offset(p) + (by * nbx + bx) * 64, where
+ *    nbx = ceil(width/8), nby = ceil(height/8) and coeff_offset(p) is the sum
+ *    of nbx*nby*64 over the planes before p in the same call.
+ */
+#ifndef DCTGB_H
+#define DCTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DCT_OK = 0,
+    DCT_ERR_INVALID_ARG = 1,   /* bad pointer, size, quality or table value */
+    DCT_ERR_UNSUPPORTED = 2,   /* valid request the library does not serve */
+    DCT_ERR_ALLOC = 3,         /* a device or host allocation failed */
+    DCT_ERR_CUDA = 4,          /* a CUDA call or launch failed */
+    DCT_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    DCT_ERR_STATE = 6          /* the plan is not in the state the call needs */
+} dct_status;
+
+typedef struct dct_plan_s* dct_plan_t;
+typedef void* dct_stream_t;    /* cudaStream_t */
+
+/* One uint8 sample plane.  `data` is a device pointer; it is read-only for
+ * inputs and written for outputs. */
+typedef struct {
+    uint8_t* data;
+    int32_t width;
+    int32_t height;
+    int32_t pitch;             /* bytes between row starts, >= width */
+} dct_plane;
+
+enum { DCT_LAYOUT_GRAY8 = 0, DCT_LAYOUT_YUV420 = 1 };
+
+/* Quality 1..100 selects the IJG-scaled T.81 Annex K tables: the luminance
+ * table for plane 0 and, under DCT_LAYOUT_YUV420, the chrominance table for
+ * planes 1 and 2.  Quality 0 means "use qtab_host", which holds 64 entries
+ * (one table for every plane) or 2*64 entries (luma table, then chroma table
+ * for planes >= 1 under DCT_LAYOUT_YUV420), natural order, each in 1..255. */
+
+typedef struct {
+    int32_t max_width;         /* largest plane width accepted, >= 1 */
+    int32_t max_height;        /* largest plane height accepted, >= 1 */
+    int32_t layout;            /* DCT_LAYOUT_GRAY8 or DCT_LAYOUT_YUV420 */
+    int32_t max_batch;         /* largest item count for the batch calls, >= 0 */
+    uint32_t flags;            /* reserved, must be 0 */
+} dct_plan_desc;
+
+/* Numeric spec compiled into the library (mirrors include/dctgb_spec.json). */
+typedef struct {
+    int32_t P;                 /* level-shift fraction bits: x = (p - 128) << P */
+    int32_t N;                 /* CORDIC micro-rotations per rotation (shifts 1..N) */
+    int32_t R;                 /* dequantiser weight fraction bits */
+    int32_t quant_shift;       /* quantiser multiplier fraction bits (32) */
+    int32_t dequant_clamp;     /* |q*Q| clamp before weighting (4096) */
+    int32_t psnr_max;          /* default MAX of Eq. 23 (255) */
+    uint32_t sigma_odd_upper;  /* bit i set <=> s_i = +1 for rot(d3,d0,3pi/16) */
+    uint32_t sigma_odd_lower;  /* same for rot(d2,d1,pi/16) */
+    uint32_t sigma_even;       /* same for the -pi/8 part of rot(e2,e3,3pi/8) */
+    int32_t stats_words;       /* uint64 words per plane written by dct_compress stats */
+} dct_spec_info;
+
+/* Fills *out with the compiled spec.  Host only; never fails for out != NULL. */
+dct_status dct_spec_query(dct_spec_info* out);
+
+/* Host only: the quantiser/dequantiser tables the device uses for one plane
+ * (Sec. 3.2 quantiser; IJG scaling of T.81 Annex K).  quality/qtab_host as
+ * above; chroma selects the chrominance table (quality > 0) or the second
+ * half of qtab_host.  Writes Q_host[64] (1..255), M_host[64] =
+ * rint(2^32 / (8 * 2^P * g_u g_v Q)), W_host[64] = rint(2^R / (g_u g_v)).
+ * Any output pointer may be NULL. */
+dct_status dct_tables(int quality, const uint16_t* qtab_host, int qtab_entries, int chroma,
+                      uint16_t* Q_host, uint32_t* M_host, int32_t* W_host);
+
+/* Creates a plan: validates the limits and allocates the plan's own device
+ * workspace (batch work list, tables, statistics scratch).  `stream` orders
+ * the workspace initialisation.  The plan is not thread-safe: one host
+ * thread at a time; calls on different streams must not overlap on the GPU
+ * when they share the plan's workspace (the batch and rate-control calls). */
+dct_status dct_plan_create(dct_plan_t* out, const dct_plan_desc* desc, dct_stream_t stream);
+
+/* Frees the plan's workspace and graphs (synchronises the device first). */
+dct_status dct_plan_destroy(dct_plan_t plan);
+
+/* Forward path (Sec. 2.5.2 transform, Sec. 3.2 quantiser): for each plane,
+ * level shift, 2-D Cordic-Loeffler DCT, quantise, store int16 coefficients.
+ *  planes[nplanes]  1..4 input planes (device data), each within the plan limits.
+ *  coeffs           device int16 output, sum over planes of nbx*nby*64 values,
+ *                   16-byte aligned.
+ *  stats_out        optional (NULL = skip) device uint64 array of
+ *                   dct_spec_info.stats_words words per plane, overwritten:
+ *                   words 0..63 band energies sum_blocks ((|Y_uv| >> P)^2),
+ *                   then pixel statistics (see dct_stats_layout in the
+ *                   Python binding): sum p, sum p^2, min p, max p,
+ *                   sum |dx|, sum |dy|, sum dx^2, sum dy^2 (within blocks),
+ *                   four counts of blocks whose AC band-energy sum is below
+ *                   2^10, 2^14, 2^18, 2^22, number of blocks, samples. */
+dct_status dct_compress(dct_plan_t plan, const dct_plane* planes, int nplanes, int quality,
+                        const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
+                        uint64_t* stats_out, dct_stream_t stream);
+
+/* Inverse path (Sec. 3.2 dequantiser and IDCT): dequantise, 2-D transposed
+ * Cordic-Loeffler graph, descale and clamp to uint8.
+ *  coeffs           device int16 input laid out as dct_compress writes it
+ *                   for planes of the sizes of out_planes, 16-byte aligned.
+ *  out_planes       nplanes output planes (device data written).
+ *  ref_planes       optional originals (same sizes) for a fused SSE; NULL = none.
+ *  sse_out          device uint64[nplanes], overwritten with
+ *                   sum (ref - out)^2 per plane (Eq. 24 numerator); required
+ *                   iff ref_planes != NULL. */
+dct_status dct_reconstruct(dct_plan_t plan, const int16_t* coeffs, const dct_plane* out_planes,
+                           int nplanes, int quality, const uint16_t* qtab_host, int qtab_entries,
+                           const dct_plane* ref_planes, uint64_t* sse_out, dct_stream_t stream);
+
+/* One pass over the pixels doing the forward path, the inverse path and the
+ * SSE (the whole Sec. 3.2 pipeline and Eq. 24) with the coefficients kept in
+ * registers.  coeffs (may be NULL) receives what dct_compress would write;
+ * recon_planes (may be NULL) receives what dct_reconstruct would write;
+ * sse_out (device uint64[nplanes], required) is overwritten with the SSE. */
+dct_status dct_codec_fused(dct_plan_t plan, const dct_plane* planes, int nplanes, int quality,
+                           const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
+                           const dct_plane* recon_planes, uint64_t* sse_out, dct_stream_t stream);
+
+/* SSE and PSNR of two sets of planes of equal sizes (Eq. 23, Eq. 24).
+ *  sse_out    device uint64[nplanes], overwritten.
+ *  psnr_host  optional host double[nplanes + 1]: per-plane PSNR and the
+ *             sample-weighted PSNR over all planes, with MAX = max_value
+ *             (0 = the spec default 255); +inf when the SSE is 0.  When it is
+ *             given the call synchronises `stream`. */
+dct_status dct_psnr(dct_plan_t plan, const dct_plane* a, const dct_plane* b, int nplanes,
+                    uint64_t* sse_out, double* psnr_host, double max_value, dct_stream_t stream);
+
+/* Host only: PSNR = 10 log10(max_value^2 * n / sse) (Eq. 23 with Eq. 24);
+ * +inf for sse == 0; max_value 0 means 255. */
+double dct_psnr_from_sse(uint64_t sse, int64_t n_samples, double max_value);
+
+/* ---------------------------------------------------------------------
+ * Batched path: many images of uneven sizes and qualities in one
+ * persistent launch replayed from a CUDA graph.
+ * --------------------------------------------------------------------- */
+
+enum {
+    DCT_OP_COMPRESS = 1u,      /* write coefficients */
+    DCT_OP_RECONSTRUCT = 2u,   /* write the reconstruction */
+    DCT_OP_SSE = 4u            /* accumulate the SSE against the source */
+};
+
+typedef struct {
+    dct_plane src;             /* input plane (device) */
+    int16_t* coeffs;           /* output coefficients or NULL (needs OP_COMPRESS) */
+    uint8_t* recon;            /* output plane data or NULL (needs OP_RECONSTRUCT) */
+    int32_t recon_pitch;       /* bytes between reconstruction rows */
+    int32_t quality;           /* 1..100, or 0 = use qtab_host of the item */
+    int32_t chroma;            /* 1 = chrominance table (quality > 0) */
+    const uint16_t* qtab_host; /* 64 entries when quality == 0, else NULL */
+} dct_batch_item;
+
+/* Launch shape of the persistent kernel, chosen by dct_autotune. */
+typedef struct {
+    int32_t threads_per_cta;   /* 64..256, multiple of 32 */
+    int32_t ctas_per_sm;       /* >= 1 */
+    int32_t tile_blocks;       /* 8x8 blocks per warp tile: 32 or 64 */
+    int32_t reserved;
+} dct_launch_shape;
+
+/* Uploads a work list of n items (1..max_batch) to the plan's workspace,
+ * builds the per-item tables and captures [clear SSE, persistent kernel]
+ * into a CUDA graph on `stream`.  ops is a mask of DCT_OP_*; with DCT_OP_SSE
+ * sse_out (device uint64[n]) receives each item's SSE.  The device pointers
+ * of the items are kept by the plan and used by every dct_batch_launch until
+ * the next dct_batch_prepare.  shape may be NULL (the plan's tuned or
+ * default shape). */
+dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n, uint32_t ops,
+                             uint64_t* sse_out, const dct_launch_shape* shape, dct_stream_t stream);
+
+/* Replays the prepared graph on `stream`.  DCT_ERR_STATE if nothing is prepared. */
+dct_status dct_batch_launch(dct_plan_t plan, dct_stream_t stream);
+
+/* Times candidate launch shapes for the prepared batch (CUDA events on
+ * `stream`, which is synchronised), keeps the fastest as the plan's shape,
+ * re-captures the graph with it and writes it to *best (may be NULL).
+ * ms_host (may be NULL) receives the best time in milliseconds. */
+dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host, dct_stream_t stream);
+
+/* Thread-local description of the last error on this thread. */
+const char* dct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCTGB_H */

@@ -1,0 +1,410 @@
+// Batched path: many planes of uneven sizes and qualities in one persistent
+// launch over a device work list, replayed from a CUDA graph, with a launch
+// shape chosen by timing candidates (dct_autotune).
+//
+// Work list: item i covers warp tiles [tile_begin[i], tile_begin[i+1]).
+// Each warp takes one contiguous range of tiles (ranges differ by at most one
+// tile), so consecutive tiles of a warp usually belong to the same item: the
+// warp keeps that item's descriptor and tables in registers / its own shared
+// memory slot and accumulates the item's SSE in a register, flushing it with
+// one atomic add when the item changes.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "host_common.h"
+
+namespace dctgb {
+
+struct BatchArgs {
+    const PlaneArg* items;      // device work list
+    const int32_t* tile_begin;  // nitems + 1 prefix offsets
+    const QuantSet* tabs;       // unique tables
+    int32_t nitems;
+    int32_t ntiles;
+};
+
+__device__ __forceinline__ int find_item(const int32_t* __restrict__ tb, int n, int tile) {
+    int lo = 0, hi = n - 1;   // largest i with tb[i] <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tb + mid) <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kBatchSlotBytes = kStageBytesPerWarp + (int)sizeof(QuantSet);
+
+template <unsigned MODE>
+__global__ void __launch_bounds__(256) k_batch(const __grid_constant__ BatchArgs args) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int warps_per_cta = blockDim.x >> 5;
+    uint8_t* slot = smem + (size_t)warp * kBatchSlotBytes;
+    QuantSet* T = reinterpret_cast<QuantSet*>(slot);
+    uint8_t* stage = slot + sizeof(QuantSet);
+
+    const long long total_warps = (long long)gridDim.x * warps_per_cta;
+    const long long gw = (long long)blockIdx.x * warps_per_cta + warp;
+    const int t_begin = (int)((gw * args.ntiles) / total_warps);
+    const int t_end = (int)(((gw + 1) * args.ntiles) / total_warps);
+
+    int cur = -1;
+    PlaneArg P;
+    unsigned long long sse = 0ull;
+    for (int tile = t_begin; tile < t_end; ++tile) {
+        if (cur < 0 || tile >= P.tile_begin + (P.nblk + kTileBlocks - 1) / kTileBlocks) {
+            if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(P.sse, sse);
+            sse = 0ull;
+            cur = find_item(args.tile_begin, args.nitems, tile);
+            P = args.items[cur];
+            __syncwarp();
+            const uint4* s = reinterpret_cast<const uint4*>(args.tabs + P.table);
+            uint4* d = reinterpret_cast<uint4*>(T);
+            for (int i = lane; i < (int)(sizeof(QuantSet) / 16); i += 32) d[i] = __ldg(s + i);
+            __syncwarp();
+        }
+        const unsigned e = process_tile<MODE>(P, *T, tile - P.tile_begin, lane, stage, P.stats);
+        sse += e;
+    }
+    if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(P.sse, sse);
+}
+
+// Clears the SSE words (and statistics, with min words set to all ones).
+__global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (do_sse) *items[i].sse = 0ull;
+        if (do_stats) {
+            unsigned long long* st = items[i].stats;
+            for (int w = 0; w < kStatsWords; ++w) st[w] = (w == kStMin) ? ~0ull : 0ull;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+using KernelPtr = void (*)(BatchArgs);
+
+static KernelPtr batch_kernel(unsigned mode) {
+    switch (mode) {
+        case kLoadPix | kStoreCoef: return k_batch<kLoadPix | kStoreCoef>;
+        case kLoadPix | kStoreCoef | kStats: return k_batch<kLoadPix | kStoreCoef | kStats>;
+        case kLoadCoef | kInverse | kStoreRecon: return k_batch<kLoadCoef | kInverse | kStoreRecon>;
+        case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch<kLoadCoef | kInverse | kStoreRecon | kSse>;
+        case kLoadPix | kInverse | kSse: return k_batch<kLoadPix | kInverse | kSse>;
+        case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch<kLoadPix | kInverse | kSse | kStoreCoef>;
+        case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch<kLoadPix | kInverse | kSse | kStoreRecon>;
+        case kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon:
+            return k_batch<kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon>;
+        case kLoadPix | kInverse | kStoreRecon: return k_batch<kLoadPix | kInverse | kStoreRecon>;
+        case kLoadPix | kInverse | kStoreCoef | kStoreRecon:
+            return k_batch<kLoadPix | kInverse | kStoreCoef | kStoreRecon>;
+        default: return nullptr;
+    }
+}
+
+struct BatchState {
+    // device workspace (capacity = plan max_batch)
+    PlaneArg* d_items = nullptr;
+    int32_t* d_tile_begin = nullptr;
+    QuantSet* d_tabs = nullptr;
+    unsigned long long* d_stats = nullptr;   // only for the rate-control helpers
+    int cap = 0;
+    // host staging (pinned)
+    PlaneArg* h_items = nullptr;
+    int32_t* h_tile_begin = nullptr;
+    QuantSet* h_tabs = nullptr;
+    // prepared launch
+    int n = 0, ntiles = 0, ntabs = 0;
+    unsigned modes[2] = {0u, 0u};   // one or two kernels (two-pass)
+    int nkernels = 0;
+    bool stats = false;
+    bool sse = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    dct_launch_shape shape{256, 0, kTileBlocks, 0};
+    bool prepared = false;
+};
+
+static void release(BatchState* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_items);
+    cudaFree(b->d_tile_begin);
+    cudaFree(b->d_tabs);
+    cudaFreeHost(b->h_items);
+    cudaFreeHost(b->h_tile_begin);
+    cudaFreeHost(b->h_tabs);
+    delete b;
+}
+
+static dct_status ensure_state(dct_plan_t plan) {
+    if (plan->batch) return DCT_OK;
+    const int cap = plan->desc.max_batch;
+    if (cap < 1) return fail(DCT_ERR_STATE, "plan was created with max_batch = 0");
+    BatchState* b = new (std::nothrow) BatchState();
+    if (!b) return fail(DCT_ERR_ALLOC, "host allocation failed");
+    b->cap = cap;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(PlaneArg) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tabs, sizeof(QuantSet) * cap);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(PlaneArg) * cap);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tile_begin, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tabs, sizeof(QuantSet) * cap);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        release(b);
+        return fail(DCT_ERR_ALLOC, std::string("batch workspace: ") + cudaGetErrorString(e));
+    }
+    plan->batch = b;
+    return DCT_OK;
+}
+
+static size_t batch_smem(int threads) { return (size_t)(threads / 32) * kBatchSlotBytes; }
+
+static int batch_grid(const dct_plan_s* plan, unsigned mode, const dct_launch_shape& sh, int ntiles) {
+    const int threads = sh.threads_per_cta;
+    int per_sm = sh.ctas_per_sm;
+    if (per_sm <= 0) {
+        int occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(mode), threads, batch_smem(threads)) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+        per_sm = occ;
+    }
+    const int warps = threads / 32;
+    const int need = std::max(1, (ntiles + warps - 1) / warps);
+    return std::min(need, plan->num_sms * per_sm);
+}
+
+// Records [init, kernel(s)] on the capture stream and instantiates the graph.
+static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
+    BatchState* b = plan->batch;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaStream_t s = b->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    if (b->sse || b->stats) {
+        const int g = std::min(1024, (b->n + 255) / 256);
+        k_batch_init<<<g, 256, 0, s>>>(b->d_items, b->n, b->sse ? 1 : 0, b->stats ? 1 : 0);
+    }
+    BatchArgs a;
+    a.items = b->d_items;
+    a.tile_begin = b->d_tile_begin;
+    a.tabs = b->d_tabs;
+    a.nitems = b->n;
+    a.ntiles = b->ntiles;
+    for (int k = 0; k < b->nkernels; ++k) {
+        KernelPtr kp = batch_kernel(b->modes[k]);
+        const size_t smem = batch_smem(sh.threads_per_cta);
+        cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kp<<<batch_grid(plan, b->modes[k], sh, b->ntiles), sh.threads_per_cta, smem, s>>>(a);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaGetLastError();
+    e = cudaStreamEndCapture(s, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e2, "batch launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b->shape = sh;
+    return DCT_OK;
+}
+
+static bool valid_shape(const dct_launch_shape& sh) {
+    return sh.threads_per_cta >= 64 && sh.threads_per_cta <= 256 && sh.threads_per_cta % 32 == 0 &&
+           sh.ctas_per_sm >= 0 && sh.ctas_per_sm <= 32 && sh.tile_blocks == kTileBlocks;
+}
+
+void batch_release(dct_plan_t plan) {
+    if (plan && plan->batch) {
+        release(plan->batch);
+        plan->batch = nullptr;
+    }
+}
+
+}  // namespace dctgb
+
+using namespace dctgb;
+
+extern "C" {
+
+dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n, uint32_t ops,
+                             uint64_t* sse_out, const dct_launch_shape* shape, dct_stream_t stream) {
+    if (!plan) return fail(DCT_ERR_INVALID_ARG, "null plan");
+    if (!items) return fail(DCT_ERR_INVALID_ARG, "null items");
+    if (n < 1 || n > plan->desc.max_batch) return fail(DCT_ERR_INVALID_ARG, "n must be 1..max_batch");
+    const uint32_t known = DCT_OP_COMPRESS | DCT_OP_RECONSTRUCT | DCT_OP_SSE;
+    if (ops == 0 || (ops & ~known)) return fail(DCT_ERR_INVALID_ARG, "ops must be a non-empty mask of DCT_OP_*");
+    if ((ops & DCT_OP_SSE) && !sse_out) return fail(DCT_ERR_INVALID_ARG, "DCT_OP_SSE needs sse_out");
+    if (sse_out && (((uintptr_t)sse_out) & 7u)) return fail(DCT_ERR_INVALID_ARG, "sse_out must be 8-byte aligned");
+    if (shape && !valid_shape(*shape)) return fail(DCT_ERR_INVALID_ARG, "invalid launch shape");
+    dct_status st = ensure_state(plan);
+    if (st != DCT_OK) return st;
+    BatchState* b = plan->batch;
+    b->prepared = false;
+
+    const bool comp = ops & DCT_OP_COMPRESS, rec = ops & DCT_OP_RECONSTRUCT, sse = ops & DCT_OP_SSE;
+    // mode selection:
+    //  COMPRESS alone             forward only (coefficients)
+    //  RECONSTRUCT without COMPRESS  inverse only from coefficients (+ SSE vs src)
+    //  COMPRESS + RECONSTRUCT/SSE  one fused pass
+    //  SSE alone                  fused pass that stores nothing
+    unsigned mode;
+    if (comp && !rec && !sse) mode = kLoadPix | kStoreCoef;
+    else if (rec && !comp) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
+    else mode = kLoadPix | kInverse | (sse ? kSse : 0u) | (comp ? kStoreCoef : 0u) | (rec ? kStoreRecon : 0u);
+
+    std::map<std::vector<uint16_t>, int> uniq;
+    int cursor = 0;
+    int ntabs = 0;
+    for (int i = 0; i < n; ++i) {
+        const dct_batch_item& it = items[i];
+        dct_plane src = it.src;
+        const bool need_src = (mode & kLoadPix) || (mode & kSse);
+        if (need_src) {
+            if ((st = check_plane(plan, src, "item src")) != DCT_OK) return st;
+        } else {
+            if (src.width < 1 || src.height < 1 || src.width > plan->desc.max_width || src.height > plan->desc.max_height)
+                return fail(DCT_ERR_INVALID_ARG, "item size outside the plan limits");
+        }
+        PlaneArg& a = b->h_items[i];
+        memset(&a, 0, sizeof a);
+        fill_plane(a, src, cursor);
+        if (cursor < 0 || cursor > (1 << 30)) return fail(DCT_ERR_INVALID_ARG, "batch too large");
+        a.src = src.data;
+        a.src_pitch = src.pitch;
+        a.ref = src.data;
+        a.ref_pitch = src.pitch;
+        int fl = 0;
+        if (src.data && (((uintptr_t)src.data) & 7u) == 0 && (src.pitch & 7) == 0) fl |= kVecSrc | kVecRef;
+        if ((mode & kStoreCoef) || (mode & kLoadCoef)) {
+            if (!it.coeffs) return fail(DCT_ERR_INVALID_ARG, "item coeffs is null");
+            if (((uintptr_t)it.coeffs) & 15u) return fail(DCT_ERR_INVALID_ARG, "item coeffs must be 16-byte aligned");
+            a.coef = it.coeffs;
+        }
+        if (mode & kStoreRecon) {
+            if (!it.recon) return fail(DCT_ERR_INVALID_ARG, "item recon is null");
+            if (it.recon_pitch < src.width) return fail(DCT_ERR_INVALID_ARG, "item recon_pitch < width");
+            a.dst = it.recon;
+            a.dst_pitch = it.recon_pitch;
+            if ((((uintptr_t)it.recon) & 7u) == 0 && (it.recon_pitch & 7) == 0) fl |= kVecDst;
+        }
+        a.flags = fl;
+        a.sse = sse ? reinterpret_cast<unsigned long long*>(sse_out) + i : nullptr;
+        if (it.quality < 0 || it.quality > 100) return fail(DCT_ERR_INVALID_ARG, "item quality must be 0..100");
+        std::vector<uint16_t> key;
+        if (it.quality > 0) {
+            key = {(uint16_t)it.quality, (uint16_t)(it.chroma ? 1 : 0)};
+        } else {
+            if (!it.qtab_host) return fail(DCT_ERR_INVALID_ARG, "item quality 0 needs qtab_host");
+            key.assign(it.qtab_host, it.qtab_host + 64);
+            key.push_back(0xFFFF);
+        }
+        auto f = uniq.find(key);
+        if (f == uniq.end()) {
+            st = build_tables(it.quality, it.qtab_host, 64, it.chroma, b->h_tabs[ntabs]);
+            if (st != DCT_OK) return st;
+            f = uniq.emplace(key, ntabs++).first;
+        }
+        a.table = f->second;
+        b->h_tile_begin[i] = a.tile_begin;
+    }
+    b->h_tile_begin[n] = cursor;
+    b->n = n;
+    b->ntiles = cursor;
+    b->ntabs = ntabs;
+    b->modes[0] = mode;
+    b->nkernels = 1;
+    b->stats = false;
+    b->sse = sse;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(PlaneArg) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tile_begin, b->h_tile_begin, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tabs, b->h_tabs, sizeof(QuantSet) * ntabs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // staging buffers are reused by the next prepare
+    if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+
+    dct_launch_shape sh = shape ? *shape : plan->shape;
+    if (!valid_shape(sh)) sh = dct_launch_shape{256, 0, kTileBlocks, 0};
+    if ((st = capture(plan, sh)) != DCT_OK) return st;
+    b->prepared = true;
+    return DCT_OK;
+}
+
+dct_status dct_batch_launch(dct_plan_t plan, dct_stream_t stream) {
+    if (!plan) return fail(DCT_ERR_INVALID_ARG, "null plan");
+    if (!plan->batch || !plan->batch->prepared) return fail(DCT_ERR_STATE, "no prepared batch");
+    cudaError_t e = cudaGraphLaunch(plan->batch->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return DCT_OK;
+}
+
+dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host, dct_stream_t stream) {
+    if (!plan) return fail(DCT_ERR_INVALID_ARG, "null plan");
+    if (!plan->batch || !plan->batch->prepared) return fail(DCT_ERR_STATE, "no prepared batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    const int threads_c[] = {64, 128, 256};
+    const int per_sm_c[] = {1, 2, 3, 4, 6, 8};
+    dct_launch_shape best_sh = plan->batch->shape;
+    float best_ms = 1e30f;
+    dct_status st = DCT_OK;
+    for (int t : threads_c) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(plan->batch->modes[0]), t, batch_smem(t));
+        for (int c : per_sm_c) {
+            if (c > occ) continue;
+            dct_launch_shape sh{t, c, kTileBlocks, 0};
+            if ((st = capture(plan, sh)) != DCT_OK) goto done;
+            for (int w = 0; w < 2; ++w) cudaGraphLaunch(plan->batch->exec, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; ++r) cudaGraphLaunch(plan->batch->exec, s);
+            cudaEventRecord(e1, s);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                st = cuda_fail(e, "autotune timing");
+                goto done;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 5.f;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_sh = sh;
+            }
+        }
+    }
+    st = capture(plan, best_sh);
+    if (st == DCT_OK) {
+        plan->shape = best_sh;
+        if (best) *best = best_sh;
+        if (ms_host) *ms_host = best_ms;
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Host-side helpers shared by the C-ABI translation units: error reporting,
+// plan layout, table construction and argument checks.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dctgb.h"
+#include "kernels.cuh"
+
+namespace dctgb {
+
+// thread-local last error
+void set_error(const std::string& msg);
+dct_status fail(dct_status st, const std::string& msg);
+dct_status cuda_fail(cudaError_t e, const char* what);
+
+// Builds Q, M, W for one plane.  quality 1..100 scales the T.81 Annex K
+// table (chroma selects K.2); quality 0 takes qtab (64 or 128 entries).
+dct_status build_tables(int quality, const uint16_t* qtab, int qtab_entries, int chroma, QuantSet& out);
+
+// Batch state lives in batch.cu; the plan only holds a pointer to it.
+struct BatchState;
+
+}  // namespace dctgb
+
+struct dct_plan_s {
+    dct_plan_desc desc;
+    int device;
+    int num_sms;
+    dct_launch_shape shape;        // batch launch shape (tuned or default)
+    dctgb::BatchState* batch;      // batch workspace and graph
+};
+
+namespace dctgb {
+
+// Checks one plane against the plan limits; `what` names it in errors.
+dct_status check_plane(const dct_plan_s* plan, const dct_plane& p, const char* what);
+
+// Fills the PlaneArg geometry fields and the running tile/coef offsets.
+void fill_plane(PlaneArg& a, const dct_plane& p, int& tile_cursor);
+
+// Frees the plan's batch workspace and graph (batch.cu).
+void batch_release(dct_plan_t plan);
+
+}  // namespace dctgb

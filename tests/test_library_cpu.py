@@ -1,0 +1,110 @@
+"""CPU checks of the C-ABI library: it builds and loads, exports every symbol
+include/dctgb.h declares, reports the spec the oracle reads, and builds the
+same quantiser/dequantiser tables as the oracle.  No GPU is touched."""
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import codec, ijg
+from oracle.cordic_loeffler import Sigmas
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(dct_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 10
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_1306_1373_gb300 import dctgb
+    assert set(dctgb.declared_symbols()) >= header_functions()
+
+
+def sigma_mask(sig):
+    return sum(1 << i for i, s in enumerate(sig, start=1) if s > 0)
+
+
+def test_spec_matches_json_and_oracle(lib):
+    from paper_1306_1373_gb300 import dctgb
+    info = dctgb.dct_spec_query()
+    spec = json.load(open(os.path.join(ROOT, "include", "dctgb_spec.json")))
+    assert info["P"] == spec["P_level_shift_bits"]
+    assert info["N"] == spec["N_cordic_iterations"]
+    assert info["R"] == spec["R_dequant_bits"]
+    assert info["quant_shift"] == spec["quant_shift_bits"]
+    assert info["dequant_clamp"] == spec["dequant_clamp"]
+    assert info["psnr_max"] == spec["psnr_max_default"]
+    s = Sigmas()
+    assert info["sigma_odd_upper"] == sigma_mask(s.odd_upper)
+    assert info["sigma_odd_lower"] == sigma_mask(s.odd_lower)
+    assert info["sigma_even"] == sigma_mask(s.even)
+    assert info["stats_words"] == 80
+
+
+@pytest.mark.parametrize("chroma", [0, 1])
+def test_tables_match_oracle_every_quality(lib, chroma):
+    from paper_1306_1373_gb300 import dctgb
+    w_or = codec.dequant_weights()
+    for q in range(1, 101):
+        Q, M, W = dctgb.dct_tables(q, chroma=chroma)
+        q_or = ijg.chroma_table(q) if chroma else ijg.luma_table(q)
+        assert (Q == q_or).all(), q
+        assert (M == codec.quant_multipliers(q_or)).all(), q
+        assert (W == w_or).all()
+
+
+def test_tables_custom(lib):
+    from paper_1306_1373_gb300 import dctgb
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        t = rng.integers(1, 256, size=64)
+        Q, M, _ = dctgb.dct_tables(0, qtab=t)
+        assert (Q.reshape(-1) == t).all()
+        assert (M == codec.quant_multipliers(t.reshape(8, 8))).all()
+    two = rng.integers(1, 256, size=128)
+    Q, _, _ = dctgb.dct_tables(0, qtab=two, chroma=1)
+    assert (Q.reshape(-1) == two[64:]).all()
+
+
+@pytest.mark.parametrize("bad", [dict(quality=101), dict(quality=-1), dict(quality=0),
+                                 dict(quality=0, qtab=[0] * 64), dict(quality=0, qtab=[256] * 64),
+                                 dict(quality=0, qtab=[5] * 63)])
+def test_tables_reject_bad_arguments(lib, bad):
+    from paper_1306_1373_gb300 import dctgb
+    with pytest.raises(dctgb.DctError) as ei:
+        dctgb.dct_tables(bad.get("quality"), qtab=bad.get("qtab"))
+    assert ei.value.status == 1
+
+
+def test_psnr_from_sse_closed_forms(lib):
+    from paper_1306_1373_gb300 import dctgb
+    assert abs(dctgb.dct_psnr_from_sse(600, 600) - 20 * math.log10(255)) < 1e-12
+    assert dctgb.dct_psnr_from_sse(0, 100) == math.inf
+    assert abs(dctgb.dct_psnr_from_sse(100, 100, 100.0) - 40.0) < 1e-12
+
+
+def test_product_path_does_not_import_oracle():
+    # the product package must not reach the oracle or carry a CPU fallback
+    pkg = os.path.join(ROOT, "paper_1306_1373_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "oracle" not in text, fn
