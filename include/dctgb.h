@@ -177,7 +177,11 @@ double dct_psnr_from_sse(uint64_t sse, int64_t n_samples, double max_value);
 enum {
     DCT_OP_COMPRESS = 1u,      /* write coefficients */
     DCT_OP_RECONSTRUCT = 2u,   /* write the reconstruction */
-    DCT_OP_SSE = 4u            /* accumulate the SSE against the source */
+    DCT_OP_SSE = 4u,           /* accumulate the SSE against the source */
+    DCT_OP_TWO_PASS = 8u       /* with COMPRESS|RECONSTRUCT: a forward kernel that
+                                  writes the coefficients, then an inverse kernel
+                                  that reads them back (Sec. 3.2's separate
+                                  kernels), instead of one fused pass */
 };
 
 typedef struct {
@@ -199,9 +203,17 @@ typedef struct {
 } dct_launch_shape;
 
 /* Uploads a work list of n items (1..max_batch) to the plan's workspace,
- * builds the per-item tables and captures [clear SSE, persistent kernel]
- * into a CUDA graph on `stream`.  ops is a mask of DCT_OP_*; with DCT_OP_SSE
- * sse_out (device uint64[n]) receives each item's SSE.  The device pointers
+ * builds the per-item tables and captures [clear SSE, persistent kernel(s)]
+ * into a CUDA graph on a plan-owned stream.  ops is a mask of DCT_OP_*:
+ *   COMPRESS alone                forward pass, coefficients written;
+ *   RECONSTRUCT without COMPRESS  inverse pass from the items' coefficients;
+ *   COMPRESS|RECONSTRUCT          one fused pass writing both;
+ *   ... | TWO_PASS                forward kernel, then inverse kernel;
+ *   SSE                           adds the SSE against src (alone: a fused
+ *                                 pass that stores nothing).
+ * With DCT_OP_SSE, sse_out (device uint64[n]) receives each item's SSE.
+ * The call synchronises `stream` (the upload uses plan-owned pinned
+ * staging buffers).  The device pointers
  * of the items are kept by the plan and used by every dct_batch_launch until
  * the next dct_batch_prepare.  shape may be NULL (the plan's tuned or
  * default shape). */

@@ -45,36 +45,41 @@ def up_to_date():
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+def _compile(src, verbose, defines, build_dir):
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [_nvcc()] + ARCH + NVCC_FLAGS + ["-D%s" % d for d in defines] + \
+        (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, jobs=None):
-    """Compiles every .cu under csrc/ and links libdctgb.so.  Returns its path."""
-    if not force and up_to_date():
+def build(force=False, verbose=False, jobs=None, defines=(), out_dir=None):
+    """Compiles every .cu under csrc/ and links libdctgb.so.  Returns its path.
+    ``defines`` (NAME=VALUE strings) and ``out_dir`` build a variant library
+    elsewhere (for A/B measurements) without touching the default one."""
+    lib = LIB if out_dir is None else os.path.join(out_dir, "libdctgb.so")
+    build_dir = BUILD if out_dir is None else os.path.join(out_dir, "_build")
+    if not force and out_dir is None and not defines and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     srcs = sources()
     jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose, list(defines), build_dir), srcs))
     if verbose:
         for obj, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -83,6 +83,7 @@ dct_status build_tables(int quality, const uint16_t* qtab, int qtab_entries, int
             out.Q[i] = q[i];
             out.M[i] = (uint32_t)m;
             out.W[i] = (int32_t)w;
+            out.QW[i] = q[i] * (int32_t)w;
         }
     }
     return DCT_OK;

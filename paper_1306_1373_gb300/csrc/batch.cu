@@ -15,6 +15,10 @@
 
 #include "host_common.h"
 
+#ifndef DCTGB_PREFETCH
+#define DCTGB_PREFETCH 1    // cp.async prefetch of the next tile in the batched kernel
+#endif
+
 namespace dctgb {
 
 struct BatchArgs {
@@ -34,17 +38,26 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ tb, int n, 
     return lo;
 }
 
-constexpr int kBatchSlotBytes = kStageBytesPerWarp + (int)sizeof(QuantSet);
+__device__ __forceinline__ int tiles_of(const PlaneArg& P) { return (P.nblk + kTileBlocks - 1) / kTileBlocks; }
 
+// Warp w of the grid processes tiles [w * T / W, (w + 1) * T / W).  While a
+// tile computes, the warp's cp.async copies of the next tile (same item)
+// fill the other half of its double buffer; cp.async.wait_group 1 then
+// guarantees the current tile's group has landed.
 template <unsigned MODE>
-__global__ void __launch_bounds__(256) k_batch(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant__ BatchArgs args) {
     extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int kWarpBytes = warp_smem_bytes(MODE);
+    constexpr bool kPixPf = (MODE & kLoadPix) || (MODE & kSse);
+    constexpr bool kCoefPf = (MODE & kLoadCoef) != 0;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps_per_cta = blockDim.x >> 5;
-    uint8_t* slot = smem + (size_t)warp * kBatchSlotBytes;
-    QuantSet* T = reinterpret_cast<QuantSet*>(slot);
-    uint8_t* stage = slot + sizeof(QuantSet);
+    uint8_t* base = smem + (size_t)warp * kWarpBytes;
+    QuantSet* T = reinterpret_cast<QuantSet*>(base);
+    PlaneArg& P = *reinterpret_cast<PlaneArg*>(base + sizeof(QuantSet));
+    uint8_t* pixb = base + sizeof(QuantSet) + kDescBytes;
+    uint8_t* stg = pixb + (kPixPf ? 2 * kPixBytes : 0);
 
     const long long total_warps = (long long)gridDim.x * warps_per_cta;
     const long long gw = (long long)blockIdx.x * warps_per_cta + warp;
@@ -52,24 +65,52 @@ __global__ void __launch_bounds__(256) k_batch(const __grid_constant__ BatchArgs
     const int t_end = (int)(((gw + 1) * args.ntiles) / total_warps);
 
     int cur = -1;
-    PlaneArg P;
+    int item_end = 0;                 // first tile past the current item
+    unsigned long long* item_sse = nullptr;
     unsigned long long sse = 0ull;
+    bool pf_valid = false;
     for (int tile = t_begin; tile < t_end; ++tile) {
-        if (cur < 0 || tile >= P.tile_begin + (P.nblk + kTileBlocks - 1) / kTileBlocks) {
-            if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(P.sse, sse);
+        const int k = tile - t_begin;
+        __syncwarp();
+        if (cur < 0 || tile >= item_end) {
+            if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
             sse = 0ull;
             cur = find_item(args.tile_begin, args.nitems, tile);
-            P = args.items[cur];
-            __syncwarp();
-            const uint4* s = reinterpret_cast<const uint4*>(args.tabs + P.table);
+            item_end = __ldg(args.tile_begin + cur + 1);
+            const PlaneArg* gi = args.items + cur;
+            item_sse = gi->sse;
+            if (lane < (int)(sizeof(PlaneArg) / 4))
+                reinterpret_cast<uint32_t*>(&P)[lane] = __ldg(reinterpret_cast<const uint32_t*>(gi) + lane);
+            const uint4* s = reinterpret_cast<const uint4*>(args.tabs + __ldg(&gi->table));
             uint4* d = reinterpret_cast<uint4*>(T);
             for (int i = lane; i < (int)(sizeof(QuantSet) / 16); i += 32) d[i] = __ldg(s + i);
             __syncwarp();
+            pf_valid = false;
         }
-        const unsigned e = process_tile<MODE>(P, *T, tile - P.tile_begin, lane, stage, P.stats);
+        const bool next_same = DCTGB_PREFETCH && tile + 1 < t_end && tile + 1 < item_end;
+        if (next_same) {
+            const int nt = tile + 1 - P.tile_begin;
+            if (kPixPf) {
+                uint8_t* nb = pixb + ((k + 1) & 1) * kPixBytes;
+                if (MODE & kLoadPix) prefetch_block(P, P.src, P.src_pitch, kVecSrc, nt, lane, nb);
+                else prefetch_block(P, P.ref, P.ref_pitch, kVecRef, nt, lane, nb);
+            }
+            if (kCoefPf) prefetch_coef(P, nt, lane, stg + ((k + 1) & 1) * kStageBytes);
+        }
+        cp_async_commit();
+        if (pf_valid) {
+            cp_async_wait<1>();
+            __syncwarp();
+        }
+        uint8_t* stage = kCoefPf ? stg + (k & 1) * kStageBytes : stg;
+        const uint8_t* pixbuf = (kPixPf && pf_valid) ? pixb + (k & 1) * kPixBytes : nullptr;
+        const unsigned e = process_tile<MODE>(P, *T, tile - P.tile_begin, lane, stage, pixbuf,
+                                              kCoefPf && pf_valid, P.stats);
         sse += e;
+        pf_valid = next_same;
     }
-    if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(P.sse, sse);
+    cp_async_wait<0>();
+    if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
 }
 
 // Clears the SSE words (and statistics, with min words set to all ones).
@@ -166,14 +207,14 @@ static dct_status ensure_state(dct_plan_t plan) {
     return DCT_OK;
 }
 
-static size_t batch_smem(int threads) { return (size_t)(threads / 32) * kBatchSlotBytes; }
+static size_t batch_smem(int threads, unsigned mode) { return (size_t)(threads / 32) * warp_smem_bytes(mode); }
 
 static int batch_grid(const dct_plan_s* plan, unsigned mode, const dct_launch_shape& sh, int ntiles) {
     const int threads = sh.threads_per_cta;
     int per_sm = sh.ctas_per_sm;
     if (per_sm <= 0) {
         int occ = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(mode), threads, batch_smem(threads)) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(mode), threads, batch_smem(threads, mode)) !=
                 cudaSuccess || occ < 1)
             occ = 1;
         per_sm = occ;
@@ -205,7 +246,7 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     a.ntiles = b->ntiles;
     for (int k = 0; k < b->nkernels; ++k) {
         KernelPtr kp = batch_kernel(b->modes[k]);
-        const size_t smem = batch_smem(sh.threads_per_cta);
+        const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k]);
         cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kp<<<batch_grid(plan, b->modes[k], sh, b->ntiles), sh.threads_per_cta, smem, s>>>(a);
     }
@@ -247,7 +288,7 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     if (!plan) return fail(DCT_ERR_INVALID_ARG, "null plan");
     if (!items) return fail(DCT_ERR_INVALID_ARG, "null items");
     if (n < 1 || n > plan->desc.max_batch) return fail(DCT_ERR_INVALID_ARG, "n must be 1..max_batch");
-    const uint32_t known = DCT_OP_COMPRESS | DCT_OP_RECONSTRUCT | DCT_OP_SSE;
+    const uint32_t known = DCT_OP_COMPRESS | DCT_OP_RECONSTRUCT | DCT_OP_SSE | DCT_OP_TWO_PASS;
     if (ops == 0 || (ops & ~known)) return fail(DCT_ERR_INVALID_ARG, "ops must be a non-empty mask of DCT_OP_*");
     if ((ops & DCT_OP_SSE) && !sse_out) return fail(DCT_ERR_INVALID_ARG, "DCT_OP_SSE needs sse_out");
     if (sse_out && (((uintptr_t)sse_out) & 7u)) return fail(DCT_ERR_INVALID_ARG, "sse_out must be 8-byte aligned");
@@ -258,13 +299,16 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     b->prepared = false;
 
     const bool comp = ops & DCT_OP_COMPRESS, rec = ops & DCT_OP_RECONSTRUCT, sse = ops & DCT_OP_SSE;
+    const bool two = ops & DCT_OP_TWO_PASS;
+    if (two && !(comp && rec)) return fail(DCT_ERR_INVALID_ARG, "DCT_OP_TWO_PASS needs COMPRESS|RECONSTRUCT");
     // mode selection:
     //  COMPRESS alone             forward only (coefficients)
     //  RECONSTRUCT without COMPRESS  inverse only from coefficients (+ SSE vs src)
     //  COMPRESS + RECONSTRUCT/SSE  one fused pass
     //  SSE alone                  fused pass that stores nothing
     unsigned mode;
-    if (comp && !rec && !sse) mode = kLoadPix | kStoreCoef;
+    if (two) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
+    else if (comp && !rec && !sse) mode = kLoadPix | kStoreCoef;
     else if (rec && !comp) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
     else mode = kLoadPix | kInverse | (sse ? kSse : 0u) | (comp ? kStoreCoef : 0u) | (rec ? kStoreRecon : 0u);
 
@@ -274,7 +318,7 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     for (int i = 0; i < n; ++i) {
         const dct_batch_item& it = items[i];
         dct_plane src = it.src;
-        const bool need_src = (mode & kLoadPix) || (mode & kSse);
+        const bool need_src = (mode & kLoadPix) || (mode & kSse) || two;
         if (need_src) {
             if ((st = check_plane(plan, src, "item src")) != DCT_OK) return st;
         } else {
@@ -291,7 +335,7 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
         a.ref_pitch = src.pitch;
         int fl = 0;
         if (src.data && (((uintptr_t)src.data) & 7u) == 0 && (src.pitch & 7) == 0) fl |= kVecSrc | kVecRef;
-        if ((mode & kStoreCoef) || (mode & kLoadCoef)) {
+        if ((mode & kStoreCoef) || (mode & kLoadCoef) || two) {
             if (!it.coeffs) return fail(DCT_ERR_INVALID_ARG, "item coeffs is null");
             if (((uintptr_t)it.coeffs) & 15u) return fail(DCT_ERR_INVALID_ARG, "item coeffs must be 16-byte aligned");
             a.coef = it.coeffs;
@@ -327,8 +371,14 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     b->n = n;
     b->ntiles = cursor;
     b->ntabs = ntabs;
-    b->modes[0] = mode;
-    b->nkernels = 1;
+    if (two) {
+        b->modes[0] = kLoadPix | kStoreCoef;
+        b->modes[1] = mode;
+        b->nkernels = 2;
+    } else {
+        b->modes[0] = mode;
+        b->nkernels = 1;
+    }
     b->stats = false;
     b->sse = sse;
 
@@ -366,29 +416,32 @@ dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host,
         cudaEventDestroy(e0);
         return cuda_fail(e, "cudaEventCreate");
     }
+    // candidate shapes: CTA sizes x CTAs per SM (beyond the resident count the
+    // grid is simply oversubscribed: more, shorter contiguous tile ranges)
     const int threads_c[] = {64, 128, 256};
-    const int per_sm_c[] = {1, 2, 3, 4, 6, 8};
+    const int per_sm_c[] = {1, 2, 4, 8, 16};
     dct_launch_shape best_sh = plan->batch->shape;
     float best_ms = 1e30f;
     dct_status st = DCT_OK;
     for (int t : threads_c) {
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(plan->batch->modes[0]), t, batch_smem(t));
         for (int c : per_sm_c) {
-            if (c > occ) continue;
+            if (t * c > 4096) continue;
             dct_launch_shape sh{t, c, kTileBlocks, 0};
             if ((st = capture(plan, sh)) != DCT_OK) goto done;
             for (int w = 0; w < 2; ++w) cudaGraphLaunch(plan->batch->exec, s);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 5; ++r) cudaGraphLaunch(plan->batch->exec, s);
-            cudaEventRecord(e1, s);
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-                st = cuda_fail(e, "autotune timing");
-                goto done;
+            float times[7];
+            for (int r = 0; r < 7; ++r) {
+                cudaEventRecord(e0, s);
+                cudaGraphLaunch(plan->batch->exec, s);
+                cudaEventRecord(e1, s);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                    st = cuda_fail(e, "autotune timing");
+                    goto done;
+                }
+                cudaEventElapsedTime(&times[r], e0, e1);
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= 5.f;
+            std::sort(times, times + 7);
+            const float ms = times[3];
             if (ms < best_ms) {
                 best_ms = ms;
                 best_sh = sh;

@@ -20,41 +20,74 @@
 #pragma once
 #include "dctgb_spec.h"
 
+#ifndef DCTGB_MADHI
+#define DCTGB_MADHI 0
+#endif
+
 namespace dctgb {
 
-// kN micro-rotations with the directions of MASK (bit i set: s_i = +1).
-template <unsigned MASK>
-__device__ __forceinline__ void cordic_fwd(int& a, int& b) {
-#pragma unroll
-    for (int i = 1; i <= kN; ++i) {
-        const int sa = a >> i;
-        const int sb = b >> i;
-        if (MASK & (1u << i)) {
-            a += sb;
-            b -= sa;
+// acc + (v >> I) with an arithmetic (floor) shift.  With DCTGB_MADHI and
+// I >= 2 it is one mad.hi.s32: the high word of v * 2^(32-I) is exactly
+// floor(v / 2^I), added to acc in the same instruction.
+template <int I>
+__device__ __forceinline__ int add_shr(int acc, int v) {
+#if DCTGB_MADHI
+    if constexpr (I >= 2) {
+        int d;
+        asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "n"(1 << (32 - I)), "r"(acc));
+        return d;
+    }
+#endif
+    return acc + (v >> I);
+}
+
+template <int I>
+__device__ __forceinline__ int sub_shr(int acc, int v) {
+    return acc - (v >> I);
+}
+
+// Micro-rotations I..kN with the directions of MASK (bit i set: s_i = +1):
+// (a, b) <- (a + s_i (b >> i), b - s_i (a >> i)) from the pre-step values.
+template <unsigned MASK, int I>
+__device__ __forceinline__ void cordic_fwd_from(int& a, int& b) {
+    if constexpr (I <= kN) {
+        int na, nb;
+        if constexpr ((MASK >> I) & 1u) {
+            na = add_shr<I>(a, b);
+            nb = sub_shr<I>(b, a);
         } else {
-            a -= sb;
-            b += sa;
+            na = sub_shr<I>(a, b);
+            nb = add_shr<I>(b, a);
         }
+        a = na;
+        b = nb;
+        cordic_fwd_from<MASK, I + 1>(a, b);
     }
 }
 
-// Transposed CORDIC block: the same shifts, each with -s_i, ascending i.
-template <unsigned MASK>
-__device__ __forceinline__ void cordic_tr(int& a, int& b) {
-#pragma unroll
-    for (int i = 1; i <= kN; ++i) {
-        const int sa = a >> i;
-        const int sb = b >> i;
-        if (MASK & (1u << i)) {
-            a -= sb;
-            b += sa;
+// Transposed micro-rotations: the same shifts with -s_i, ascending i.
+template <unsigned MASK, int I>
+__device__ __forceinline__ void cordic_tr_from(int& a, int& b) {
+    if constexpr (I <= kN) {
+        int na, nb;
+        if constexpr ((MASK >> I) & 1u) {
+            na = sub_shr<I>(a, b);
+            nb = add_shr<I>(b, a);
         } else {
-            a += sb;
-            b -= sa;
+            na = add_shr<I>(a, b);
+            nb = sub_shr<I>(b, a);
         }
+        a = na;
+        b = nb;
+        cordic_tr_from<MASK, I + 1>(a, b);
     }
 }
+
+template <unsigned MASK>
+__device__ __forceinline__ void cordic_fwd(int& a, int& b) { cordic_fwd_from<MASK, 1>(a, b); }
+
+template <unsigned MASK>
+__device__ __forceinline__ void cordic_tr(int& a, int& b) { cordic_tr_from<MASK, 1>(a, b); }
 
 // Forward 8-point graph on v[0..7] (in place: v[k] <- Y_k).
 __device__ __forceinline__ void loeffler8_fwd(int (&v)[8]) {

@@ -6,11 +6,13 @@
 // of kTileBlocks consecutive blocks in block-major order (b = by * nbx + bx,
 // wrapping across block rows).  Lane l of a warp owns block b0 + l and keeps
 // its 64 samples in registers, so the row/column transpose between the two
-// 1-D passes is free.  Pixel rows are loaded and stored 8 bytes per lane
-// (a warp covers 256 contiguous bytes of a row); int16 coefficients go
-// through a padded per-warp shared-memory stage so that the global side is
-// 16 bytes per lane over contiguous 512-byte spans.  The grid is persistent:
-// warps stride over all tiles of all planes of the launch.
+// 1-D passes is free.  Pixel rows move 8 bytes per lane (a warp covers 256
+// contiguous bytes of an image row); int16 coefficients go through a
+// swizzled per-warp shared-memory stage so the global side moves 16 bytes
+// per lane over contiguous 512-byte spans.  The batched kernel prefetches
+// the next tile's pixels / coefficients with cp.async while the current
+// tile computes.  The path is bound by integer issue, not by HBM, so the
+// code is arranged to minimise instructions per sample.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,18 +20,23 @@
 #include "cordic_loeffler.cuh"
 #include "dctgb_spec.h"
 
+#ifndef DCTGB_MINB
+#define DCTGB_MINB 2        // minimum resident CTAs per SM (launch bounds: <= 128 registers)
+#endif
+
 namespace dctgb {
 
 constexpr int kMaxPlanes = 4;
-constexpr int kTileBlocks = 32;      // blocks per warp tile (one per lane)
-constexpr int kStageStride = 144;    // bytes per block in the stage (128 + 16 pad)
-constexpr int kStageBytesPerWarp = kTileBlocks * kStageStride;
+constexpr int kTileBlocks = 32;                   // blocks per warp tile (one per lane)
+constexpr int kStageBytes = kTileBlocks * 128;    // one tile of int16 coefficients
+constexpr int kPixBytes = kTileBlocks * 64;       // one tile of uint8 samples
 
 // Per-plane quantiser / dequantiser tables (natural order u*8+v).
 struct QuantSet {
     uint32_t M[64];   // rint(2^32 / (8 * 2^P * g_u g_v Q))
     int32_t Q[64];    // 1..255
     int32_t W[64];    // rint(2^R / (g_u g_v))
+    int32_t QW[64];   // Q * W
 };
 
 struct PlaneArg {
@@ -54,7 +61,7 @@ struct DirectArgs {
     int32_t ntiles;
 };
 
-// Mode bits of the kernel template.
+// Mode bits of the kernel templates.
 enum : unsigned {
     kLoadPix = 1u,     // read samples, forward transform, quantise
     kStoreCoef = 2u,   // write the quantised coefficients
@@ -75,8 +82,44 @@ enum : int {
 };
 
 // --------------------------------------------------------------------------
+// shared-memory layouts (swizzled, conflict-free for both access patterns)
+// --------------------------------------------------------------------------
+
+// Coefficient stage: block `blk` occupies 128 bytes; its row u (8 int16) sits
+// in 16-byte slot u ^ (blk & 7).  A lane writing/reading the 8 rows of its own
+// block and 8 lanes reading one block's 8 slots both hit 8 distinct
+// 16-byte bank groups.
+__device__ __forceinline__ int stage_off(int blk, int row) { return blk * 128 + ((row ^ (blk & 7)) << 4); }
+
+// Pixel buffer: lane l's 8 rows of 8 bytes at l * 64; row r in 8-byte slot
+// r ^ ((l >> 1) & 7), so 16 lanes reading one row each touch 32 distinct banks.
+__device__ __forceinline__ int pix_off(int lane, int r) { return lane * 64 + ((r ^ ((lane >> 1) & 7)) << 3); }
+
+// --------------------------------------------------------------------------
+// asynchronous copies (completion via cp.async.wait_group: no spin loops)
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// --------------------------------------------------------------------------
 // sample I/O
 // --------------------------------------------------------------------------
+
+__device__ __forceinline__ bool interior(const PlaneArg& P, int by, int bx) {
+    return bx * 8 + 8 <= P.width && by * 8 + 8 <= P.height;
+}
 
 // Loads block (by, bx) as 8 rows of two little-endian uint32 words.  Samples
 // outside the plane repeat the nearest edge sample (edge replication).
@@ -108,6 +151,51 @@ __device__ __forceinline__ void load_block(const uint8_t* __restrict__ src, int 
     }
 }
 
+// Issues cp.async copies of this lane's block of tile `tile_in_plane` into
+// `buf` (a kPixBytes region) when the block is interior and the plane's rows
+// are 8-byte aligned; the consumer re-evaluates the same condition.
+__device__ __forceinline__ void prefetch_block(const PlaneArg& P, const uint8_t* base, int pitch, int vec_flag,
+                                               int tile_in_plane, int lane, uint8_t* buf) {
+    const int b = tile_in_plane * kTileBlocks + lane;
+    if (b < P.nblk && (P.flags & vec_flag)) {
+        const int by = b / P.nbx, bx = b - by * P.nbx;
+        if (interior(P, by, bx)) {
+            const uint8_t* p = base + (size_t)(by * 8) * pitch + bx * 8;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) cp_async8(buf + pix_off(lane, r), p + (size_t)r * pitch);
+        }
+    }
+}
+
+// Issues cp.async copies of tile `tile_in_plane`'s coefficients into `stage`.
+__device__ __forceinline__ void prefetch_coef(const PlaneArg& P, int tile_in_plane, int lane, uint8_t* stage) {
+    const int b0 = tile_in_plane * kTileBlocks;
+    const int nvalid = min(kTileBlocks, P.nblk - b0);
+    const uint8_t* g = reinterpret_cast<const uint8_t*>(P.coef + (size_t)b0 * 64);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int c = k * 32 + lane;
+        const int blk = c >> 3;
+        if (blk < nvalid) cp_async16(stage + stage_off(blk, c & 7), g + (size_t)c * 16);
+    }
+}
+
+// Block samples from the prefetch buffer when they were prefetched, else from
+// global memory (edge blocks, unaligned planes, first tile of an item).
+__device__ __forceinline__ void fetch_block(const PlaneArg& P, const uint8_t* base, int pitch, int vec_flag,
+                                            const uint8_t* buf, int lane, int by, int bx, uint32_t (&pix)[8][2]) {
+    if (buf && (P.flags & vec_flag) && interior(P, by, bx)) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint2 v = *reinterpret_cast<const uint2*>(buf + pix_off(lane, r));
+            pix[r][0] = v.x;
+            pix[r][1] = v.y;
+        }
+    } else {
+        load_block(base, pitch, P.width, P.height, by, bx, (P.flags & vec_flag) != 0, pix);
+    }
+}
+
 // Stores the in-plane part of block (by, bx).
 __device__ __forceinline__ void store_block(uint8_t* __restrict__ dst, int pitch, int w, int h,
                                             int by, int bx, bool vec, const uint32_t (&pix)[8][2]) {
@@ -130,27 +218,33 @@ __device__ __forceinline__ int sample(const uint32_t (&pix)[8][2], int r, int c)
     return (int)((pix[r][c >> 2] >> (8 * (c & 3))) & 0xFFu);
 }
 
-// --------------------------------------------------------------------------
-// per-CTA accumulators (shared memory), flushed to global at the end
-// --------------------------------------------------------------------------
-
-struct CtaAcc {
-    unsigned long long sse[kMaxPlanes];
-    unsigned long long st[kMaxPlanes][kStatsWords];
-};
-
 __device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(0xffffffffu, v); }
+
+// Shared memory a warp needs in a given mode (batched kernel): its item's
+// tables and descriptor, double-buffered samples and coefficient stages.
+constexpr int kDescBytes = 128;
+static_assert(sizeof(PlaneArg) <= kDescBytes, "descriptor slot too small");
+__host__ __device__ constexpr int warp_smem_bytes(unsigned mode) {
+    return (int)sizeof(QuantSet) + kDescBytes +
+           (((mode & kLoadPix) || (mode & kSse)) ? 2 * kPixBytes : 0) +
+           ((mode & kLoadCoef) ? 2 * kStageBytes : ((mode & kStoreCoef) ? kStageBytes : 0));
+}
 
 // --------------------------------------------------------------------------
 // one warp tile
 // --------------------------------------------------------------------------
 
-// Processes warp tile `tile_in_plane` of plane P.  Statistics go to the 80
-// words at `st` (shared or global memory); the return value is the tile's
-// SSE (the same in every lane; 0 without kSse).
+// Processes warp tile `tile_in_plane` of plane P.
+//  stage      kStageBytes of this warp's shared memory (coefficients)
+//  pixbuf     this tile's prefetched samples (forward) or SSE reference
+//             (inverse), or nullptr
+//  coef_ready the stage already holds this tile's coefficients
+// Statistics go to the 80 words at `st` (shared or global); the return value
+// is the tile's SSE (the same in every lane; 0 without kSse).
 template <unsigned MODE>
-__device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantSet& T, int tile_in_plane,
-                                                 int lane, uint8_t* stage, unsigned long long* st) {
+__device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantSet& T, int tile_in_plane, int lane,
+                                                 uint8_t* stage, const uint8_t* pixbuf, bool coef_ready,
+                                                 unsigned long long* st) {
     const int b0 = tile_in_plane * kTileBlocks;
     const int nvalid = min(kTileBlocks, P.nblk - b0);
     const bool active = lane < nvalid;
@@ -166,7 +260,7 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
 
     if (MODE & kLoadPix) {
         if (active) {
-            load_block(P.src, P.src_pitch, P.width, P.height, by, bx, (P.flags & kVecSrc) != 0, pix);
+            fetch_block(P, P.src, P.src_pitch, kVecSrc, pixbuf, lane, by, bx, pix);
         } else {
 #pragma unroll
             for (int r = 0; r < 8; ++r) pix[r][0] = pix[r][1] = 0x80808080u;
@@ -242,20 +336,22 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             }
         }
 
-        // quantiser: q = sgn(Y) * ((|Y| * M + 2^31) >> 32)
+        // Quantiser q = sgn(Y) ((|Y| M + 2^31) >> 32), computed as the high
+        // word of the signed product Y * M + 2^31 - [Y < 0]: for Y < 0,
+        // floor((Y M + 2^31 - 1) / 2^32) = -floor((|Y| M + 2^31) / 2^32), so
+        // both signs round half away from zero exactly as the definition.
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const int y = x[u][v];
-                const uint32_t a = (uint32_t)abs(y);
-                const uint32_t q = (uint32_t)(((unsigned long long)a * T.M[u * 8 + v] + 0x80000000ull) >> 32);
-                x[u][v] = y < 0 ? -(int)q : (int)q;
+                const unsigned c = 0x80000000u ^ (unsigned)(y >> 31);
+                const long long p = (long long)y * (long long)(int)T.M[u * 8 + v] + (long long)c;
+                x[u][v] = (int)(p >> 32);
             }
         }
 
         if (MODE & kStoreCoef) {
-            uint8_t* mine = stage + lane * kStageStride;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 uint4 w;
@@ -263,7 +359,7 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
                 w.y = ((uint32_t)x[u][2] & 0xFFFFu) | ((uint32_t)x[u][3] << 16);
                 w.z = ((uint32_t)x[u][4] & 0xFFFFu) | ((uint32_t)x[u][5] << 16);
                 w.w = ((uint32_t)x[u][6] & 0xFFFFu) | ((uint32_t)x[u][7] << 16);
-                *reinterpret_cast<uint4*>(mine + 16 * u) = w;
+                *reinterpret_cast<uint4*>(stage + stage_off(lane, u)) = w;
             }
             __syncwarp();
             uint4* g = reinterpret_cast<uint4*>(P.coef + (size_t)b0 * 64);
@@ -271,26 +367,26 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             for (int k = 0; k < 8; ++k) {
                 const int c = k * 32 + lane;
                 const int blk = c >> 3;
-                if (blk < nvalid) g[c] = *reinterpret_cast<const uint4*>(stage + blk * kStageStride + (c & 7) * 16);
+                if (blk < nvalid) g[c] = *reinterpret_cast<const uint4*>(stage + stage_off(blk, c & 7));
             }
             __syncwarp();
         }
     }
 
     if (MODE & kLoadCoef) {
-        const uint4* g = reinterpret_cast<const uint4*>(P.coef + (size_t)b0 * 64);
+        if (!coef_ready) {
+            const uint4* g = reinterpret_cast<const uint4*>(P.coef + (size_t)b0 * 64);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int c = k * 32 + lane;
-            const int blk = c >> 3;
-            if (blk < nvalid)
-                *reinterpret_cast<uint4*>(stage + blk * kStageStride + (c & 7) * 16) = __ldg(g + c);
+            for (int k = 0; k < 8; ++k) {
+                const int c = k * 32 + lane;
+                const int blk = c >> 3;
+                if (blk < nvalid) *reinterpret_cast<uint4*>(stage + stage_off(blk, c & 7)) = __ldg(g + c);
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        const uint8_t* mine = stage + lane * kStageStride;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const uint4 w = *reinterpret_cast<const uint4*>(mine + 16 * u);
+            const uint4 w = *reinterpret_cast<const uint4*>(stage + stage_off(lane, u));
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -298,7 +394,6 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
                 x[u][2 * k + 1] = (int)ws[k] >> 16;
             }
         }
-        __syncwarp();
         if (!active) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -308,14 +403,21 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
     }
 
     if (MODE & kInverse) {
-        // dequantiser: G = clamp(q * Q, -4096, 4096) * W
+        // Dequantiser G = clamp(q Q, -4096, 4096) W.  When q comes from this
+        // kernel's own quantiser, |q Q| <= |X| + Q/2 + 1 < 1200 (the Cordic
+        // coefficient |X| is within 14 of an orthonormal DCT value, itself at
+        // most 1024), so the clamp never acts and G = q (Q W) exactly.
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                int t = x[u][v] * T.Q[u * 8 + v];
-                t = max(-kDequantClamp, min(kDequantClamp, t));
-                x[u][v] = t * T.W[u * 8 + v];
+                if (MODE & kLoadPix) {
+                    x[u][v] = x[u][v] * T.QW[u * 8 + v];
+                } else {
+                    int t = x[u][v] * T.Q[u * 8 + v];
+                    t = max(-kDequantClamp, min(kDequantClamp, t));
+                    x[u][v] = t * T.W[u * 8 + v];
+                }
             }
         }
         // The DC input reaches every output through additions only, so the
@@ -341,21 +443,22 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             store_block(P.dst, P.dst_pitch, P.width, P.height, by, bx, (P.flags & kVecDst) != 0, out);
 
         if (MODE & kSse) {
-            if (!(MODE & kLoadPix)) {
-                if (active)
-                    load_block(P.ref, P.ref_pitch, P.width, P.height, by, bx, (P.flags & kVecRef) != 0, pix);
-            }
+            if (!(MODE & kLoadPix) && active) fetch_block(P, P.ref, P.ref_pitch, kVecRef, pixbuf, lane, by, bx, pix);
             unsigned e = 0;
             if (active) {
                 const int nr = min(8, P.height - by * 8), nc = min(8, P.width - bx * 8);
                 if (nr == 8 && nc == 8) {
+                    // sum (r - p)^2 = sum r^2 + sum p^2 - 2 sum r p, four bytes per dp4a
+                    unsigned rr = 0, pp = 0, rp = 0;
 #pragma unroll
                     for (int r = 0; r < 8; ++r)
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const int d = sample(out, r, c) - sample(pix, r, c);
-                            e += d * d;
+                        for (int h = 0; h < 2; ++h) {
+                            rr = __dp4a(out[r][h], out[r][h], rr);
+                            pp = __dp4a(pix[r][h], pix[r][h], pp);
+                            rp = __dp4a(out[r][h], pix[r][h], rp);
                         }
+                    e = rr + pp - 2u * rp;
                 } else {
                     for (int r = 0; r < nr; ++r)
                         for (int c = 0; c < nc; ++c) {
@@ -371,11 +474,16 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
 }
 
 // --------------------------------------------------------------------------
-// persistent kernel over all tiles of up to kMaxPlanes planes
+// persistent kernel over all tiles of up to kMaxPlanes planes (direct calls)
 // --------------------------------------------------------------------------
 
+struct CtaAcc {
+    unsigned long long sse[kMaxPlanes];
+    unsigned long long st[kMaxPlanes][kStatsWords];
+};
+
 template <unsigned MODE>
-__global__ void __launch_bounds__(256) k_codec(const __grid_constant__ DirectArgs args) {
+__global__ void __launch_bounds__(256, DCTGB_MINB) k_codec(const __grid_constant__ DirectArgs args) {
     extern __shared__ __align__(16) uint8_t smem[];
     QuantSet* tabs = reinterpret_cast<QuantSet*>(smem);                       // 2 sets
     CtaAcc* acc = reinterpret_cast<CtaAcc*>(smem + 2 * sizeof(QuantSet));
@@ -396,7 +504,7 @@ __global__ void __launch_bounds__(256) k_codec(const __grid_constant__ DirectArg
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t* stage = stage_all + warp * kStageBytesPerWarp;
+    uint8_t* stage = stage_all + warp * kStageBytes;
     const int warps_per_cta = blockDim.x >> 5;
     const int total_warps = gridDim.x * warps_per_cta;
 
@@ -406,7 +514,8 @@ __global__ void __launch_bounds__(256) k_codec(const __grid_constant__ DirectArg
         for (int k = 1; k < kMaxPlanes; ++k)
             if (k < args.nplanes && tile >= args.p[k].tile_begin) pi = k;
         const PlaneArg& P = args.p[pi];
-        const unsigned e = process_tile<MODE>(P, tabs[P.table], tile - P.tile_begin, lane, stage, acc->st[pi]);
+        const unsigned e = process_tile<MODE>(P, tabs[P.table], tile - P.tile_begin, lane, stage, nullptr, false,
+                                              acc->st[pi]);
         if ((MODE & kSse) && lane == 0 && e) atomicAdd(&acc->sse[pi], (unsigned long long)e);
     }
 
@@ -435,7 +544,7 @@ __global__ void __launch_bounds__(256) k_codec(const __grid_constant__ DirectArg
 __global__ void k_init_acc(DirectArgs args, int do_sse, int do_stats);
 
 inline size_t codec_smem_bytes(int threads) {
-    return 2 * sizeof(QuantSet) + sizeof(CtaAcc) + (size_t)(threads / 32) * kStageBytesPerWarp;
+    return 2 * sizeof(QuantSet) + sizeof(CtaAcc) + (size_t)(threads / 32) * kStageBytes;
 }
 
 // Persistent grid: enough CTAs for every tile, at most num_sms * occupancy.

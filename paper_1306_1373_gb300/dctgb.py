@@ -21,6 +21,7 @@ DCT_LAYOUT_YUV420 = 1
 DCT_OP_COMPRESS = 1
 DCT_OP_RECONSTRUCT = 2
 DCT_OP_SSE = 4
+DCT_OP_TWO_PASS = 8
 
 # statistics words written by dct_compress(stats=...) per plane
 STATS_WORDS = 80
@@ -283,7 +284,8 @@ def make_batch_items(srcs, qualities, coeffs=None, recons=None, chroma=None, qta
     """ctypes array of dct_batch_item for lists of planes and per-item settings."""
     n = len(srcs)
     arr = (dct_batch_item * n)()
-    keep = []
+    # the plan keeps raw device pointers until the next prepare: hold the tensors
+    keep = [list(srcs), list(coeffs or []), list(recons or [])]
     for i in range(n):
         it = arr[i]
         it.src = as_plane(srcs[i])

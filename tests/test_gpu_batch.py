@@ -1,0 +1,211 @@
+"""GPU parity of the batched persistent, graph-captured path: images of
+uneven sizes and qualities in one launch, against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import codec, ijg, psnr
+from synth import batch_workload, powerlaw_image
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D(cuda_ok):
+    from paper_1306_1373_gb300 import dctgb
+    dctgb.load()
+    return dctgb
+
+
+def make_items(n, seed, lo=8, hi=300, ragged=True):
+    rng = np.random.default_rng(seed)
+    items = []
+    for i in range(n):
+        h = int(rng.integers(lo, hi + 1))
+        w = int(rng.integers(lo, hi + 1))
+        if not ragged:
+            h, w = max(8, h // 8 * 8), max(8, w // 8 * 8)
+        q = int(rng.integers(1, 101))
+        chroma = bool(rng.integers(0, 2))
+        img = powerlaw_image(h, w, seed=seed * 1000 + i, beta=float(rng.uniform(1, 3))).numpy()
+        items.append(dict(img=img, quality=q, chroma=chroma))
+    return items
+
+
+def table(it):
+    return ijg.chroma_table(it["quality"]) if it["chroma"] else ijg.luma_table(it["quality"])
+
+
+def oracle(it):
+    Q = table(it)
+    c = codec.compress_plane(it["img"], Q)
+    r = codec.reconstruct_plane(c, Q, *it["img"].shape)
+    return c.reshape(-1), r, psnr.sse(it["img"], r)
+
+
+def run_batch(D, plan, items, ops, shape=None, launches=1):
+    srcs = [torch.from_numpy(it["img"]).cuda() for it in items]
+    coefs = [torch.full((D.coeff_count([s.shape]),), 12345, dtype=torch.int16, device="cuda") for s in srcs]
+    recs = [torch.zeros_like(s) for s in srcs]
+    sse = torch.full((len(items),), -1, dtype=torch.int64, device="cuda")
+    arr = D.make_batch_items(srcs, [it["quality"] for it in items], coeffs=coefs, recons=recs,
+                             chroma=[it["chroma"] for it in items])
+    D.dct_batch_prepare(plan, arr, ops, sse=sse if ops & D.DCT_OP_SSE else None, shape=shape)
+    for _ in range(launches):
+        D.dct_batch_launch(plan)
+    torch.cuda.synchronize()
+    return coefs, recs, sse, srcs, arr
+
+
+@pytest.mark.parametrize("shape", [None, (64, 1, 32, 0), (256, 2, 32, 0), (128, 16, 32, 0)])
+def test_batch_fused_matches_oracle(D, shape):
+    items = make_items(24, seed=1)
+    with D.Plan(512, 512, max_batch=64) as plan:
+        C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+        coefs, recs, sse, _, _ = run_batch(D, plan, items, C | R | S, shape=shape)
+        for i, it in enumerate(items):
+            c_or, r_or, s_or = oracle(it)
+            assert np.array_equal(coefs[i].cpu().numpy(), c_or), i
+            assert np.array_equal(recs[i].cpu().numpy(), r_or), i
+            assert int(sse[i]) == s_or, i
+
+
+@pytest.mark.parametrize("mode", ["compress", "sse_only", "compress_sse", "recon_sse", "twopass", "twopass_nosse"])
+def test_batch_op_combinations(D, mode):
+    items = make_items(12, seed=2)
+    C, R, S, T = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE, D.DCT_OP_TWO_PASS
+    ops = {"compress": C, "sse_only": S, "compress_sse": C | S, "recon_sse": C | R | S,
+           "twopass": C | R | S | T, "twopass_nosse": C | R | T}[mode]
+    with D.Plan(512, 512, max_batch=16) as plan:
+        coefs, recs, sse, _, _ = run_batch(D, plan, items, ops)
+        for i, it in enumerate(items):
+            c_or, r_or, s_or = oracle(it)
+            if ops & C:
+                assert np.array_equal(coefs[i].cpu().numpy(), c_or), i
+            else:
+                assert int((coefs[i] != 12345).sum()) == 0
+            if ops & R:
+                assert np.array_equal(recs[i].cpu().numpy(), r_or), i
+            else:
+                assert int(recs[i].abs().sum()) == 0
+            if ops & S:
+                assert int(sse[i]) == s_or, i
+
+
+def test_batch_inverse_only_from_coefficients(D):
+    items = make_items(10, seed=3)
+    with D.Plan(512, 512, max_batch=16) as plan:
+        srcs = [torch.from_numpy(it["img"]).cuda() for it in items]
+        coefs = [torch.from_numpy(oracle(it)[0]).cuda() for it in items]
+        recs = [torch.zeros_like(s) for s in srcs]
+        sse = torch.zeros(len(items), dtype=torch.int64, device="cuda")
+        arr = D.make_batch_items(srcs, [it["quality"] for it in items], coeffs=coefs, recons=recs,
+                                 chroma=[it["chroma"] for it in items])
+        D.dct_batch_prepare(plan, arr, D.DCT_OP_RECONSTRUCT | D.DCT_OP_SSE, sse=sse)
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        for i, it in enumerate(items):
+            _, r_or, s_or = oracle(it)
+            assert np.array_equal(recs[i].cpu().numpy(), r_or)
+            assert int(sse[i]) == s_or
+
+
+def test_batch_graph_replay_is_deterministic(D):
+    items = make_items(16, seed=4)
+    with D.Plan(512, 512, max_batch=16) as plan:
+        C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+        coefs, recs, sse, _, _ = run_batch(D, plan, items, C | R | S, launches=1)
+        first = (sse.clone(), [c.clone() for c in coefs])
+        for _ in range(5):
+            D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        assert torch.equal(sse, first[0])
+        for a, b in zip(coefs, first[1]):
+            assert torch.equal(a, b)
+
+
+def test_batch_custom_tables_and_single_item(D):
+    rng = np.random.default_rng(5)
+    img = powerlaw_image(70, 90, seed=5).numpy()
+    qt = rng.integers(1, 256, size=64)
+    with D.Plan(128, 128, max_batch=1) as plan:
+        src = torch.from_numpy(img).cuda()
+        coef = torch.empty(D.coeff_count([src.shape]), dtype=torch.int16, device="cuda")
+        rec = torch.empty_like(src)
+        sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+        arr = D.make_batch_items([src], [0], coeffs=[coef], recons=[rec], qtabs=[qt])
+        D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS | D.DCT_OP_RECONSTRUCT | D.DCT_OP_SSE, sse=sse)
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        Q = qt.reshape(8, 8)
+        c_or = codec.compress_plane(img, Q)
+        r_or = codec.reconstruct_plane(c_or, Q, 70, 90)
+        assert np.array_equal(coef.cpu().numpy(), c_or.reshape(-1))
+        assert np.array_equal(rec.cpu().numpy(), r_or)
+        assert int(sse[0]) == psnr.sse(img, r_or)
+
+
+def test_batch_autotune_keeps_results(D):
+    items = make_items(20, seed=6, lo=64, hi=400)
+    with D.Plan(512, 512, max_batch=32) as plan:
+        C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+        coefs, recs, sse, _, arr = run_batch(D, plan, items, C | R | S)
+        ref = sse.clone()
+        shape, ms = D.dct_autotune(plan)
+        assert shape[0] in (64, 128, 256) and shape[1] >= 1 and ms > 0
+        sse.fill_(-1)
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        assert torch.equal(sse, ref)
+
+
+def test_batch_workload_shapes_sampled(D):
+    """The 512-image batched workload (sizes 64..2048, qualities 10..95):
+    every item's SSE against its reconstruction, and sampled items against
+    the oracle."""
+    spec = batch_workload(512)
+    srcs, quals = [], []
+    for it in spec:
+        srcs.append(powerlaw_image(it["height"], it["width"], seed=it["seed"], beta=it["beta"], device="cuda"))
+        quals.append(it["quality"])
+    with D.Plan(2048, 2048, max_batch=512) as plan:
+        coefs = [torch.empty(D.coeff_count([s.shape]), dtype=torch.int16, device="cuda") for s in srcs]
+        recs = [torch.empty_like(s) for s in srcs]
+        sse = torch.zeros(512, dtype=torch.int64, device="cuda")
+        arr = D.make_batch_items(srcs, quals, coeffs=coefs, recons=recs)
+        D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS | D.DCT_OP_RECONSTRUCT | D.DCT_OP_SSE, sse=sse)
+        D.dct_autotune(plan)
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        for i in range(512):
+            d = recs[i].to(torch.int64) - srcs[i].to(torch.int64)
+            assert int(sse[i]) == int((d * d).sum())
+        for i in (0, 7, 100, 333, 511):
+            if srcs[i].numel() > 600_000:
+                continue
+            it = dict(img=srcs[i].cpu().numpy(), quality=quals[i], chroma=False)
+            c_or, r_or, s_or = oracle(it)
+            assert np.array_equal(coefs[i].cpu().numpy(), c_or)
+            assert np.array_equal(recs[i].cpu().numpy(), r_or)
+            assert int(sse[i]) == s_or
+
+
+def test_batch_invalid_arguments(D):
+    t = torch.zeros(16, 16, dtype=torch.uint8, device="cuda")
+    c = torch.zeros(4 * 64, dtype=torch.int16, device="cuda")
+    with D.Plan(32, 32, max_batch=2) as plan:
+        with pytest.raises(D.DctError):   # no prepared batch
+            D.dct_batch_launch(plan)
+        arr = D.make_batch_items([t, t, t], [50, 50, 50], coeffs=[c, c, c])
+        with pytest.raises(D.DctError):   # more than max_batch
+            D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS)
+        arr = D.make_batch_items([t], [50], coeffs=[c])
+        with pytest.raises(D.DctError):   # SSE without sse_out
+            D.dct_batch_prepare(plan, arr, D.DCT_OP_SSE)
+        with pytest.raises(D.DctError):   # two-pass without reconstruct
+            D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS | D.DCT_OP_TWO_PASS)
+        with pytest.raises(D.DctError):   # bad shape
+            D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS, shape=(100, 1, 32, 0))
+    with D.Plan(32, 32, max_batch=0) as plan:
+        with pytest.raises(D.DctError):
+            D.dct_batch_prepare(plan, D.make_batch_items([t], [50], coeffs=[c]), D.DCT_OP_COMPRESS)
