@@ -7,6 +7,9 @@ launch.  The default workload is an 8192 x 8192 grey plane plus a
 3840 x 2160 YCbCr 4:2:0 frame (luma and chroma tables, quality 75), 1/f^2
 noise with step edges: 79.55 M uint8 samples per step.
 
+Also measures learned rate control against plain 8-step bisection on the
+20,000-image grey set and the 2,000-frame 4:2:0 stream ("ratecontrol").
+
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 (the reference arm of this build) on bounded samples of the same workload.
 Multi-GPU: replicas only (every rank runs the same workload independently,
@@ -40,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default=None, help="threads,ctas_per_sm: fixed launch shape, no autotuning")
+    ap.add_argument("--no-ratecontrol", action="store_true", help="skip the learned-rate-control workloads")
+    ap.add_argument("--rc-epochs", type=int, default=300)
     return ap.parse_args()
 
 
@@ -230,6 +235,85 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# learned rate control vs bisection
+# ---------------------------------------------------------------------------
+
+def _rc_summary(ev, n_train, train_s, label_s, hist, unit):
+    out = {"unit": unit, "train_frames": n_train, "train_s": train_s, "label_s": label_s,
+           "final_train_loss": hist[-1] if hist else None}
+    for name in ("learned", "bisection"):
+        r = dict(ev[name])
+        r.pop("result")
+        out[name] = r
+    out["speedup_wall"] = ev["learned"]["frames_per_s"] / ev["bisection"]["frames_per_s"]
+    out["speedup_gpu"] = ev["learned"]["gpu_frames_per_s"] / ev["bisection"]["gpu_frames_per_s"]
+    return out
+
+
+def rc_grey(dev, epochs):
+    """20,000 seeded grey images (W, H multiples of 8 in 256..1024, 1/f^beta
+    noise with beta in 1..3 plus edges and rectangles), targets uniform in
+    28..42 dB: train on 16,000 (bisection labels), evaluate on 4,000."""
+    import torch
+    from paper_1306_1373_gb300 import dctgb as D, rc
+    from synth import powerlaw_image, ratecontrol_workload
+    spec = ratecontrol_workload(20000)
+    imgs = [powerlaw_image(it["height"], it["width"], seed=it["seed"], beta=it["beta"], rects=-1, device=dev)
+            for it in spec]
+    targets = [it["target"] for it in spec]
+    n_tr = 16000
+    with D.Plan(1024, 1024, max_batch=20000) as plan:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q_tr, _ = rc.label_by_bisection(plan, imgs[:n_tr], 1, targets[:n_tr])
+        label_s = time.perf_counter() - t0
+        feats = D.dct_rate_features(plan, imgs, 1, targets)
+        t0 = time.perf_counter()
+        net, hist = rc.train_network(feats[:n_tr].contiguous(), q_tr, epochs=epochs, batch=256, lr=2e-3, seed=0)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        ev = rc.evaluate(plan, imgs[n_tr:], 1, targets[n_tr:], net)
+    out = _rc_summary(ev, n_tr, train_s, label_s, hist, "images/s")
+    out["workload"] = "20,000 grey 256..1024 images, targets 28..42 dB, 16,000 train / 4,000 eval"
+    out["eval_megasamples"] = sum(int(t.numel()) for t in imgs[n_tr:]) / 1e6
+    return out
+
+
+def rc_stream(dev, epochs):
+    """2,000 YCbCr 4:2:0 frames (1280x720, 1920x1080, 3840x2160), targets
+    uniform in 30..40 dB; the network is trained on 600 other frames of the
+    same mix labelled by bisection."""
+    import torch
+    from paper_1306_1373_gb300 import dctgb as D, rc
+    from synth import stream_workload, yuv420_frame
+
+    def frames(spec):
+        planes = []
+        for it in spec:
+            planes.extend(yuv420_frame(it["width"], it["height"], seed=it["seed"], beta=it["beta"], device=dev))
+        return planes, [it["target"] for it in spec]
+
+    train_p, train_t = frames(stream_workload(600, seed=40))
+    eval_p, eval_t = frames(stream_workload(2000, seed=4))
+    with D.Plan(3840, 2160, max_batch=6000, layout=D.DCT_LAYOUT_YUV420) as plan:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q_tr, _ = rc.label_by_bisection(plan, train_p, 3, train_t)
+        label_s = time.perf_counter() - t0
+        feats = D.dct_rate_features(plan, train_p, 3, train_t)
+        t0 = time.perf_counter()
+        net, hist = rc.train_network(feats, q_tr, epochs=epochs, batch=64, lr=2e-3, seed=1)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del train_p
+        ev = rc.evaluate(plan, eval_p, 3, eval_t, net)
+    out = _rc_summary(ev, 600, train_s, label_s, hist, "frames/s")
+    out["workload"] = "2,000 YCbCr 4:2:0 frames 720p/1080p/2160p, targets 30..40 dB (600 other frames for training)"
+    out["eval_megasamples"] = sum(int(t.numel()) for t in eval_p) / 1e6
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -369,6 +453,10 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(planes[0].cpu().numpy(), args.cpu_seconds)
     plan.close()
+    if not args.no_ratecontrol:
+        del planes, coefs, recons, flush
+        torch.cuda.empty_cache()
+        line["ratecontrol"] = {"grey": rc_grey(dev, args.rc_epochs), "stream420": rc_stream(dev, args.rc_epochs)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -229,6 +229,107 @@ dct_status dct_batch_launch(dct_plan_t plan, dct_stream_t stream);
  * ms_host (may be NULL) receives the best time in milliseconds. */
 dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host, dct_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Learned rate control.  The paper has no rate controller; these calls
+ * choose the quality factor of the plain pipeline above for a target PSNR
+ * (Eq. 23): a small network predicts it from statistics the forward pass
+ * gathers, the pipeline verifies it, and an 8-step bisection over the
+ * qualities 1..100 is the fallback.
+ * --------------------------------------------------------------------- */
+
+#define DCT_MLP_INPUTS 80
+#define DCT_MLP_HIDDEN 64
+#define DCT_MLP_PARAMS 9409   /* 64*80 + 64 + 64*64 + 64 + 64 + 1 */
+
+/* Network 80 -> 64 -> 64 -> 1: a1 = W1 xn + b1, h1 = act(gelu(a1)),
+ * a2 = W2 h1 + b2, h2 = act(gelu(a2)), y = sigmoid(W3 h2 + b3), with
+ * xn = (x - feat_mean) / feat_std, gelu(a) = a Phi(a) and act() rounding to
+ * bfloat16 (act_bf16 = 1) or the identity.  y predicts (Q* - 1) / 99; the
+ * quality is clamp(rint(1 + 99 y), 1, 100).  All arrays are device float32
+ * owned by the caller. */
+typedef struct {
+    float* params;        /* DCT_MLP_PARAMS: W1[64][80], b1[64], W2[64][64], b2[64], W3[64], b3 */
+    float* adam_m;        /* DCT_MLP_PARAMS, Adam first moments (training only) */
+    float* adam_v;        /* DCT_MLP_PARAMS, Adam second moments (training only) */
+    float* feat_mean;     /* DCT_MLP_INPUTS */
+    float* feat_std;      /* DCT_MLP_INPUTS */
+    int32_t step;         /* Adam steps taken (dct_mlp_adam increments it) */
+    int32_t act_bf16;     /* 1: bfloat16 hidden activations, 0: float32 */
+} dct_mlp;
+
+/* 80 features per frame from dct_compress-style statistics words (device
+ * uint64, DCT stats_words per frame), the frame size and its target PSNR
+ * (device arrays of n entries): log band energies, pixel and gradient
+ * statistics, low-energy block fractions, log2 sizes, the target and a bias
+ * term (see oracle/features.py for the exact formulas). */
+dct_status dct_features(const uint64_t* stats, const int32_t* width, const int32_t* height, const float* target,
+                        int n, float* feats_out, dct_stream_t stream);
+
+/* Sets feat_mean / feat_std to the mean and standard deviation (floored at
+ * 1e-6) of each feature over n rows of feats (device, n x 80). */
+dct_status dct_mlp_set_norm(dct_mlp* net, const float* feats, int n, dct_stream_t stream);
+
+/* Forward pass for n rows: y_out (device float[n], may be NULL) and
+ * quality_out (device int32[n], may be NULL). */
+dct_status dct_mlp_forward(const dct_mlp* net, const float* feats, int n, float* y_out, int32_t* quality_out,
+                           dct_stream_t stream);
+
+/* Bytes of device workspace dct_mlp_loss_grad needs for a minibatch of `batch` rows. */
+size_t dct_mlp_workspace_bytes(int batch);
+
+/* Mean squared error over the minibatch rows index[0..batch) of (feats,
+ * labels) and its gradient (device float[DCT_MLP_PARAMS], overwritten).
+ * loss_out: device float[1].  Sums over the minibatch run in a fixed order,
+ * so the result is deterministic.  workspace: dct_mlp_workspace_bytes(batch). */
+dct_status dct_mlp_loss_grad(const dct_mlp* net, const float* feats, const float* labels, const int32_t* index,
+                             int batch, float* grad_out, float* loss_out, void* workspace, dct_stream_t stream);
+
+/* One Adam update of net->params from grad (Kingma and Ba, bias-corrected);
+ * increments net->step (host field). */
+dct_status dct_mlp_adam(dct_mlp* net, const float* grad, float lr, float beta1, float beta2, float eps,
+                        dct_stream_t stream);
+
+/* One epoch of minibatch training: for each consecutive `batch` rows of
+ * order[0..n) (device int32, a permutation chosen by the caller) a
+ * loss_grad + adam step.  loss_out: device float[ceil(n / batch)].
+ * workspace: dct_mlp_workspace_bytes(batch) + DCT_MLP_PARAMS floats. */
+dct_status dct_mlp_train_epoch(dct_mlp* net, const float* feats, const float* labels, const int32_t* order, int n,
+                               int batch, float lr, float* loss_out, void* workspace, dct_stream_t stream);
+
+/* Result summary of dct_rate_control. */
+typedef struct {
+    int32_t frames;        /* frames processed */
+    int32_t fell_back;     /* frames that went through the bisection */
+    int32_t unreachable;   /* frames whose PSNR at quality 100 is below the target */
+    int32_t within_tol;    /* frames whose final PSNR is within 0.25 dB of the target */
+    int32_t passes;        /* full-pipeline passes over frames (sum over frames) */
+    float gpu_ms;          /* device time of the call (CUDA events on `stream`) */
+} dct_rc_summary;
+
+/* Quality per frame for a target PSNR.  planes holds nframes * planes_per_frame
+ * device planes, frame-major; planes_per_frame is 1 (grey) or 3 (4:2:0: the
+ * chrominance table for planes 1 and 2).  A frame's PSNR is Eq. 23 over all
+ * of its samples with MAX 255.  With net == NULL every frame is bisected
+ * (8 passes: lo = 1, hi = 100, mid = (lo + hi) / 2, hi = mid if
+ * PSNR(mid) >= target else lo = mid + 1; the result is hi).  With a network,
+ * the statistics pass, features and network give a quality, one pass
+ * verifies it, and frames whose PSNR misses the target by more than 0.25 dB
+ * (either way) fall back to the bisection.  Decisions compare the integer
+ * SSE with thresholds computed on the host in float64.  Host outputs
+ * (nframes entries each, any may be NULL): quality_host, sse_host (SSE at
+ * the chosen quality), fell_back_host.  Synchronises `stream`.  Uses the
+ * plan's workspace: nframes * planes_per_frame <= max_batch. */
+dct_status dct_rate_control(dct_plan_t plan, const dct_plane* planes, int planes_per_frame, int nframes,
+                            const float* target_host, const dct_mlp* net, int32_t* quality_host,
+                            uint64_t* sse_host, uint8_t* fell_back_host, dct_rc_summary* summary,
+                            dct_stream_t stream);
+
+/* Features (device float[nframes * 80]) of each frame's plane 0 for the given
+ * targets: the statistics pass of dct_rate_control on its own, for training
+ * and inspection.  Same plane layout as dct_rate_control. */
+dct_status dct_rate_features(dct_plan_t plan, const dct_plane* planes, int planes_per_frame, int nframes,
+                             const float* target_host, float* feats_out, dct_stream_t stream);
+
 /* Thread-local description of the last error on this thread. */
 const char* dct_last_error(void);
 

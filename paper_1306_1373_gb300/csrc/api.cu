@@ -194,6 +194,7 @@ dct_status dct_plan_create(dct_plan_t* out, const dct_plan_desc* desc, dct_strea
     p->shape.tile_blocks = kTileBlocks;
     p->shape.reserved = 0;
     p->batch = nullptr;
+    p->rc = nullptr;
     *out = p;
     return DCT_OK;
 }
@@ -202,6 +203,7 @@ dct_status dct_plan_destroy(dct_plan_t plan) {
     if (!plan) return fail(DCT_ERR_INVALID_ARG, "null plan");
     cudaDeviceSynchronize();
     batch_release(plan);
+    rc_release(plan);
     delete plan;
     return DCT_OK;
 }

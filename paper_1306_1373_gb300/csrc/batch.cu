@@ -134,6 +134,7 @@ static KernelPtr batch_kernel(unsigned mode) {
     switch (mode) {
         case kLoadPix | kStoreCoef: return k_batch<kLoadPix | kStoreCoef>;
         case kLoadPix | kStoreCoef | kStats: return k_batch<kLoadPix | kStoreCoef | kStats>;
+        case kLoadPix | kStats: return k_batch<kLoadPix | kStats>;
         case kLoadCoef | kInverse | kStoreRecon: return k_batch<kLoadCoef | kInverse | kStoreRecon>;
         case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch<kLoadCoef | kInverse | kStoreRecon | kSse>;
         case kLoadPix | kInverse | kSse: return k_batch<kLoadPix | kInverse | kSse>;
@@ -268,6 +269,25 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
 static bool valid_shape(const dct_launch_shape& sh) {
     return sh.threads_per_cta >= 64 && sh.threads_per_cta <= 256 && sh.threads_per_cta % 32 == 0 &&
            sh.ctas_per_sm >= 0 && sh.ctas_per_sm <= 32 && sh.tile_blocks == kTileBlocks;
+}
+
+cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* tile_begin, const QuantSet* tabs,
+                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s) {
+    KernelPtr kp = batch_kernel(mode);
+    if (!kp) return cudaErrorInvalidValue;
+    dct_launch_shape sh = plan->shape;
+    if (!valid_shape(sh)) sh = dct_launch_shape{256, 0, kTileBlocks, 0};
+    const size_t smem = batch_smem(sh.threads_per_cta, mode);
+    cudaError_t e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BatchArgs a;
+    a.items = items;
+    a.tile_begin = tile_begin;
+    a.tabs = tabs;
+    a.nitems = nitems;
+    a.ntiles = ntiles;
+    kp<<<batch_grid(plan, mode, sh, ntiles), sh.threads_per_cta, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 void batch_release(dct_plan_t plan) {

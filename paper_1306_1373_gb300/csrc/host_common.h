@@ -20,8 +20,10 @@ dct_status cuda_fail(cudaError_t e, const char* what);
 // table (chroma selects K.2); quality 0 takes qtab (64 or 128 entries).
 dct_status build_tables(int quality, const uint16_t* qtab, int qtab_entries, int chroma, QuantSet& out);
 
-// Batch state lives in batch.cu; the plan only holds a pointer to it.
+// Batch and rate-control state live in batch.cu / ratecontrol.cu; the plan
+// only holds pointers to them.
 struct BatchState;
+struct RcState;
 
 }  // namespace dctgb
 
@@ -31,6 +33,7 @@ struct dct_plan_s {
     int num_sms;
     dct_launch_shape shape;        // batch launch shape (tuned or default)
     dctgb::BatchState* batch;      // batch workspace and graph
+    dctgb::RcState* rc;            // rate-control workspace
 };
 
 namespace dctgb {
@@ -43,5 +46,18 @@ void fill_plane(PlaneArg& a, const dct_plane& p, int& tile_cursor);
 
 // Frees the plan's batch workspace and graph (batch.cu).
 void batch_release(dct_plan_t plan);
+
+// Launches the batched persistent kernel of `mode` over a device work list
+// (no graph), with the plan's launch shape (batch.cu).
+cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* tile_begin, const QuantSet* tabs,
+                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s);
+
+// Frees the plan's rate-control workspace (ratecontrol.cu).
+void rc_release(dct_plan_t plan);
+
+// Network kernels (mlp.cu).
+cudaError_t launch_features(const unsigned long long* stats, const int* w, const int* h, const float* t, int n,
+                            float* out, cudaStream_t s);
+cudaError_t launch_mlp_forward(const dct_mlp* net, const float* feats, int n, float* y, int* q, cudaStream_t s);
 
 }  // namespace dctgb

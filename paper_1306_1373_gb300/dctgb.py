@@ -63,6 +63,22 @@ class dct_launch_shape(ctypes.Structure):
                 ("tile_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+DCT_MLP_INPUTS = 80
+DCT_MLP_HIDDEN = 64
+DCT_MLP_PARAMS = 9409
+
+
+class dct_mlp(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("feat_mean", ctypes.c_void_p), ("feat_std", ctypes.c_void_p), ("step", ctypes.c_int32),
+                ("act_bf16", ctypes.c_int32)]
+
+
+class dct_rc_summary(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int32), ("fell_back", ctypes.c_int32), ("unreachable", ctypes.c_int32),
+                ("within_tol", ctypes.c_int32), ("passes", ctypes.c_int32), ("gpu_ms", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _U16P = ctypes.POINTER(ctypes.c_uint16)
 _SIGNATURES = {
@@ -84,6 +100,21 @@ _SIGNATURES = {
                                          ctypes.POINTER(dct_launch_shape), _P]),
     "dct_batch_launch": (ctypes.c_int, [_P, _P]),
     "dct_autotune": (ctypes.c_int, [_P, ctypes.POINTER(dct_launch_shape), ctypes.POINTER(ctypes.c_float), _P]),
+    "dct_features": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P, _P]),
+    "dct_mlp_set_norm": (ctypes.c_int, [ctypes.POINTER(dct_mlp), _P, ctypes.c_int, _P]),
+    "dct_mlp_forward": (ctypes.c_int, [ctypes.POINTER(dct_mlp), _P, ctypes.c_int, _P, _P, _P]),
+    "dct_mlp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int]),
+    "dct_mlp_loss_grad": (ctypes.c_int, [ctypes.POINTER(dct_mlp), _P, _P, _P, ctypes.c_int, _P, _P, _P, _P]),
+    "dct_mlp_adam": (ctypes.c_int, [ctypes.POINTER(dct_mlp), _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, _P]),
+    "dct_mlp_train_epoch": (ctypes.c_int, [ctypes.POINTER(dct_mlp), _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_float, _P, _P, _P]),
+    "dct_rate_control": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(dct_mlp),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(dct_rc_summary), _P]),
+    "dct_rate_features": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_float), _P, _P]),
     "dct_last_error": (ctypes.c_char_p, []),
 }
 
@@ -330,6 +361,110 @@ def psnr_list_from_sse(sse_values, shapes, max_value=0.0):
     return out
 
 
-__all__ = [n for n in dir() if n.startswith("dct_")] + ["Plan", "load", "DctError", "as_plane", "coeff_count",
+# ---------------------------------------------------------------------------
+# learned rate control
+# ---------------------------------------------------------------------------
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Mlp:
+    """Device-resident network 80 -> 64 -> 64 -> 1 (dct_mlp) with its Adam
+    state and input normalisation, as torch float32 tensors."""
+
+    def __init__(self, params, act_bf16=True, device="cuda"):
+        p = torch.as_tensor(np.asarray(params, dtype=np.float32)).to(device)
+        if p.numel() != DCT_MLP_PARAMS:
+            raise ValueError("expected %d parameters" % DCT_MLP_PARAMS)
+        self.params = p.contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.mean = torch.zeros(DCT_MLP_INPUTS, dtype=torch.float32, device=device)
+        self.std = torch.ones(DCT_MLP_INPUTS, dtype=torch.float32, device=device)
+        self.c = dct_mlp(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.mean.data_ptr(),
+                         self.std.data_ptr(), 0, 1 if act_bf16 else 0)
+        self._ws = None
+        self._ws_batch = 0
+
+    @property
+    def step(self):
+        return self.c.step
+
+    def workspace(self, batch):
+        if self._ws is None or self._ws_batch < batch:
+            nbytes = load().dct_mlp_workspace_bytes(int(batch)) + 4 * DCT_MLP_PARAMS
+            self._ws = torch.empty((nbytes + 3) // 4, dtype=torch.float32, device=self.params.device)
+            self._ws_batch = batch
+        return self._ws
+
+    def set_norm(self, feats, stream=None):
+        _check(load().dct_mlp_set_norm(ctypes.byref(self.c), _vp(feats), int(feats.shape[0]), _stream_ptr(stream)))
+
+    def forward(self, feats, stream=None):
+        n = int(feats.shape[0])
+        y = torch.empty(n, dtype=torch.float32, device=feats.device)
+        q = torch.empty(n, dtype=torch.int32, device=feats.device)
+        _check(load().dct_mlp_forward(ctypes.byref(self.c), _vp(feats), n, _vp(y), _vp(q), _stream_ptr(stream)))
+        return y, q
+
+    def loss_grad(self, feats, labels, index, stream=None):
+        grad = torch.empty(DCT_MLP_PARAMS, dtype=torch.float32, device=feats.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feats.device)
+        ws = self.workspace(int(index.numel()))
+        _check(load().dct_mlp_loss_grad(ctypes.byref(self.c), _vp(feats), _vp(labels), _vp(index), int(index.numel()),
+                                        _vp(grad), _vp(loss), _vp(ws), _stream_ptr(stream)))
+        return loss, grad
+
+    def adam(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(load().dct_mlp_adam(ctypes.byref(self.c), _vp(grad), float(lr), float(beta1), float(beta2), float(eps),
+                                   _stream_ptr(stream)))
+
+    def train_epoch(self, feats, labels, order, batch=256, lr=1e-3, stream=None):
+        n = int(order.numel())
+        losses = torch.empty((n + batch - 1) // batch, dtype=torch.float32, device=feats.device)
+        ws = self.workspace(batch)
+        _check(load().dct_mlp_train_epoch(ctypes.byref(self.c), _vp(feats), _vp(labels), _vp(order), n, int(batch),
+                                          float(lr), _vp(losses), _vp(ws), _stream_ptr(stream)))
+        return losses
+
+
+def dct_features(stats, width, height, target, stream=None):
+    n = int(width.numel())
+    out = torch.empty(n, DCT_MLP_INPUTS, dtype=torch.float32, device=stats.device)
+    _check(load().dct_features(_vp(stats), _vp(width), _vp(height), _vp(target), n, _vp(out), _stream_ptr(stream)))
+    return out
+
+
+def dct_rate_features(plan, planes, planes_per_frame, targets, stream=None):
+    """Features (n, 80) of every frame's plane 0; planes frame-major."""
+    nf = len(planes) // planes_per_frame
+    t = (ctypes.c_float * nf)(*[float(v) for v in targets])
+    out = torch.empty(nf, DCT_MLP_INPUTS, dtype=torch.float32, device=planes[0].device)
+    _check(load().dct_rate_features(plan.handle, _planes(planes), int(planes_per_frame), nf, t, _vp(out),
+                                    _stream_ptr(stream)))
+    return out
+
+
+def dct_rate_control(plan, planes, planes_per_frame, targets, net=None, stream=None):
+    """Quality per frame for the target PSNRs (bisection when net is None).
+    Returns a dict of numpy arrays and the summary."""
+    nf = len(planes) // planes_per_frame
+    t = (ctypes.c_float * nf)(*[float(v) for v in targets])
+    q = np.zeros(nf, dtype=np.int32)
+    sse = np.zeros(nf, dtype=np.uint64)
+    fell = np.zeros(nf, dtype=np.uint8)
+    summ = dct_rc_summary()
+    _check(load().dct_rate_control(plan.handle, _planes(planes), int(planes_per_frame), nf, t,
+                                   ctypes.byref(net.c) if net is not None else None,
+                                   q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   sse.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   fell.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(summ),
+                                   _stream_ptr(stream)))
+    return dict(quality=q, sse=sse, fell_back=fell,
+                summary={f: getattr(summ, f) for f, _ in dct_rc_summary._fields_})
+
+
+__all__ = [n for n in dir() if n.startswith("dct_")] + ["Plan", "Mlp", "load", "DctError", "as_plane", "coeff_count",
                                                           "make_batch_items", "STATS_LAYOUT", "STATS_WORDS"]
 _ = math  # noqa

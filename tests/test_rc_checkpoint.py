@@ -1,0 +1,35 @@
+"""Network checkpoints: round trip and corruption detection (CPU only)."""
+import numpy as np
+import pytest
+import torch
+
+
+def test_checkpoint_round_trip_and_checksum(tmp_path):
+    from paper_1306_1373_gb300 import dctgb as D, rc
+    net = D.Mlp(rc.init_params(3), act_bf16=True, device="cpu")
+    net.m.normal_()
+    net.v.uniform_()
+    net.mean.fill_(0.5)
+    net.std.fill_(2.0)
+    net.c.step = 17
+    p = tmp_path / "net.bin"
+    rc.save(net, str(p), seed=3)
+    back = rc.load(str(p), device="cpu")
+    for a, b in ((net.params, back.params), (net.m, back.m), (net.v, back.v), (net.mean, back.mean),
+                 (net.std, back.std)):
+        assert torch.equal(a, b)
+    assert back.step == 17 and back.c.act_bf16 == 1
+    data = bytearray(p.read_bytes())
+    data[100] ^= 0xFF
+    p.write_bytes(bytes(data))
+    with pytest.raises(ValueError):
+        rc.load(str(p), device="cpu")
+
+
+def test_init_params_layout_and_seed():
+    from paper_1306_1373_gb300 import rc
+    from oracle import mlp
+    a = rc.init_params(5)
+    assert a.shape == (9409,) and a.dtype == np.float32
+    assert np.array_equal(a, rc.init_params(5)) and not np.array_equal(a, rc.init_params(6))
+    assert np.allclose(a, mlp.init_params(5), atol=1e-7)   # same seeded draw as the oracle's initialiser
