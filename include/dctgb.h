@@ -330,6 +330,29 @@ dct_status dct_rate_control(dct_plan_t plan, const dct_plane* planes, int planes
 dct_status dct_rate_features(dct_plan_t plan, const dct_plane* planes, int planes_per_frame, int nframes,
                              const float* target_host, float* feats_out, dct_stream_t stream);
 
+/* Runs one batch like dct_batch_prepare + dct_batch_launch, same item
+ * fields and ops, same results, without allocating anything: no
+ * cudaMalloc, cudaFree, pinned buffers or plan.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * while they run: processes whose device memory another allocator reserved
+ * up front, latency-critical loops that cannot absorb the implicit device
+ * synchronisation of cudaMalloc / cudaFree, and deployments with a fixed
+ * memory budget that forbid allocation after start-up.
+ *  - The work list goes to a fixed array inside the library image
+ *    (about 70 KB on every device that loads the library, held until the
+ *    process exits).  n is limited to 1..64 items; larger n returns
+ *    DCT_ERR_INVALID_ARG.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the array and overwrites it.  Calls that
+ *    overlap on the GPU (different streams, or host threads racing) race on
+ *    it: serialise them.  sse_out is cleared by the call itself.
+ *  - The descriptors are copied from the caller's stack with
+ *    cudaMemcpyAsync on `stream` (pageable: the call returns once they are
+ *    staged). */
+dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, uint32_t ops, uint64_t* sse_out,
+                                 dct_stream_t stream);
+
 /* Thread-local description of the last error on this thread. */
 const char* dct_last_error(void);
 

@@ -115,6 +115,7 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(dct_rc_summary), _P]),
     "dct_rate_features": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_float), _P, _P]),
+    "dct_batch_run_noalloc": (ctypes.c_int, [ctypes.POINTER(dct_batch_item), ctypes.c_int, ctypes.c_uint32, _P, _P]),
     "dct_last_error": (ctypes.c_char_p, []),
 }
 
@@ -344,6 +345,15 @@ def dct_batch_prepare(plan, items, ops, sse=None, shape=None, stream=None):
 
 def dct_batch_launch(plan, stream=None):
     _check(load().dct_batch_launch(plan.handle, _stream_ptr(stream)))
+
+
+def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
+    """One batch of at most 64 items through the allocation-free entry
+    point (the work list lives in a fixed array inside the library)."""
+    arr, _ = items
+    _check(load().dct_batch_run_noalloc(arr, len(arr), int(ops),
+                                        ctypes.c_void_p(sse.data_ptr()) if sse is not None else None,
+                                        _stream_ptr(stream)))
 
 
 def dct_autotune(plan, stream=None):
