@@ -93,6 +93,20 @@ def make_planes(device):
     return [grey, y, cb, cr], [False, False, True, True]
 
 
+def algorithmic_ops_per_sample():
+    """Integer operations the spec defines per sample for the whole path:
+    level shift (2), two forward 8-point passes of 21 + 12 N operations per
+    8 samples (20 butterfly adds, 1 negation, 3 CORDIC rotations of N
+    micro-rotations of 2 shifts + 2 adds), quantiser (5: |Y|, multiply,
+    rounding add, shift, sign), dequantiser (4: multiply, 2 clamps,
+    multiply), two inverse passes (same count), descale (5: rounding add,
+    shift, +128, 2 clamps) and the SSE term (3: subtract, multiply, add)."""
+    from paper_1306_1373_gb300 import dctgb as D
+    n = D.dct_spec_query()["N"]
+    per_pass = (21 + 12 * n) / 8.0
+    return 2 + 2 * per_pass + 5 + 4 + 2 * per_pass + 5 + 3
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_1373_gb300", "csrc")
@@ -362,12 +376,14 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
         D.dct_batch_launch(plan)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -413,27 +429,35 @@ def main():
         e2e = {"value": samples * world / (e2e_ms * 1e-3) / 1e6, "unit": "MPix/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel.  The path is bound by integer
+    # instruction issue (ncu: ALU and FMA-heavy pipes ~70%, DRAM ~20%), so
+    # the roofline is the int32 issue peak; the HBM fraction is reported too.
     import json as _json
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = _json.load(open(pk))
     hbm = float(peaks.get("hbm_gbs", 6780.0))
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sms * 4 * 32 * sm_mhz_max * 1e6 / 1e12          # Tops/s: 4 schedulers x 32 lanes per SM
+    ops = algorithmic_ops_per_sample()
+    bytes_per_sample = 4 if args.path == "fused" else 7
     if args.path == "fused":
         kernel = "k_batch<fused: load, fwd, quant, store coef, dequant, inv, store recon, SSE>"
-        bytes_per_sample = 4      # 1 read + 2 coefficient write + 1 reconstruction write
-        kernel_ms = ms
         note = "event interval per step covers the SSE-clear kernel (about 1%) and the fused kernel"
     else:
         kernel = "k_batch<two-pass: forward + inverse>"
-        bytes_per_sample = 7
-        kernel_ms = ms
         note = "event interval per step covers the SSE-clear, forward and inverse kernels"
-    achieved = samples * bytes_per_sample / (kernel_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": stored_traffic(kernel, WORKLOAD), "kernel": kernel,
-            "bytes_per_sample": bytes_per_sample, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+    achieved_ops = ops * samples / (ms * 1e-3) / 1e12
+    achieved_gbs = samples * bytes_per_sample / (ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak, "unit": "Tops/s (int32)",
+            "frac": achieved_ops / alu_peak, "traffic": stored_traffic(kernel, WORKLOAD), "kernel": kernel,
+            "ops_per_sample": ops,
+            "peak_source": "derived: %d SMs x 4 schedulers x 1 warp instruction (32 int32 lanes) per clock "
+                           "x %.0f MHz (sm_max_mhz)" % (n_sms, sm_mhz_max),
+            "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+                    "bytes_per_sample": bytes_per_sample, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"},
             "note": note}
 
     line = {"metric": "MPix/s DCT+quant+IDCT+PSNR", "value": value, "unit": "MPix/s", "n_gpus": world,
@@ -446,7 +470,7 @@ def main():
                        "l2": "flushed between timed steps (inputs 79.6 MB < 129 MB L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "psnr_db": {"grey": psnrs[0], "Y": psnrs[1], "Cb": psnrs[2], "Cr": psnrs[3]},
-            "roofline": roof, "clocks": clk,
+            "hbm_frac": roof["hbm"]["frac"], "roofline": roof, "clocks": clk,
             "gpu_launches": args.steps * (3 if args.path == "twopass" else 2)}
     if e2e:
         line["e2e"] = e2e
