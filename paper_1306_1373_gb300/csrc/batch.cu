@@ -40,6 +40,25 @@ __device__ __forceinline__ int find_item(const int32_t* __restrict__ tb, int n, 
 
 __device__ __forceinline__ int tiles_of(const PlaneArg& P) { return (P.nblk + kTileBlocks - 1) / kTileBlocks; }
 
+// warp-private statistics accumulator: cleared when a warp starts an item,
+// added to the item's global words (atomics) when it leaves it
+__device__ __forceinline__ void clear_stats(unsigned long long* wst, int lane) {
+    for (int w = lane; w < kStatsWords; w += 32) wst[w] = (w == kStMin) ? ~0ull : 0ull;
+    __syncwarp();
+}
+__device__ __forceinline__ void flush_stats(const unsigned long long* wst, unsigned long long* g, int lane) {
+    for (int w = lane; w < kStatsWords; w += 32) {
+        const unsigned long long v = wst[w];
+        if (w == kStMin) {
+            if (v != ~0ull) atomicMin(g + w, v);
+        } else if (w == kStMax) {
+            atomicMax(g + w, v);
+        } else if (v) {
+            atomicAdd(g + w, v);
+        }
+    }
+}
+
 // Warp w of the grid processes tiles [w * T / W, (w + 1) * T / W).  While a
 // tile computes, the warp's cp.async copies of the next tile (same item)
 // fill the other half of its double buffer; cp.async.wait_group 1 then
@@ -56,7 +75,8 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
     uint8_t* base = smem + (size_t)warp * kWarpBytes;
     QuantSet* T = reinterpret_cast<QuantSet*>(base);
     PlaneArg& P = *reinterpret_cast<PlaneArg*>(base + sizeof(QuantSet));
-    uint8_t* pixb = base + sizeof(QuantSet) + kDescBytes;
+    unsigned long long* wst = reinterpret_cast<unsigned long long*>(base + sizeof(QuantSet) + kDescBytes);
+    uint8_t* pixb = base + sizeof(QuantSet) + kDescBytes + ((MODE & kStats) ? kStatBytes : 0);
     uint8_t* stg = pixb + (kPixPf ? 2 * kPixBytes : 0);
 
     const long long total_warps = (long long)gridDim.x * warps_per_cta;
@@ -74,6 +94,8 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
         __syncwarp();
         if (cur < 0 || tile >= item_end) {
             if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
+            if ((MODE & kStats) && cur >= 0) flush_stats(wst, P.stats, lane);
+            if (MODE & kStats) clear_stats(wst, lane);
             sse = 0ull;
             cur = find_item(args.tile_begin, args.nitems, tile);
             item_end = __ldg(args.tile_begin + cur + 1);
@@ -105,12 +127,16 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
         uint8_t* stage = kCoefPf ? stg + (k & 1) * kStageBytes : stg;
         const uint8_t* pixbuf = (kPixPf && pf_valid) ? pixb + (k & 1) * kPixBytes : nullptr;
         const unsigned e = process_tile<MODE>(P, *T, tile - P.tile_begin, lane, stage, pixbuf,
-                                              kCoefPf && pf_valid, P.stats);
+                                              kCoefPf && pf_valid, wst);
         sse += e;
         pf_valid = next_same;
     }
     cp_async_wait<0>();
     if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
+    if ((MODE & kStats) && cur >= 0) {
+        __syncwarp();
+        flush_stats(wst, P.stats, lane);
+    }
 }
 
 // Clears the SSE words (and statistics, with min words set to all ones).
@@ -133,8 +159,8 @@ using KernelPtr = void (*)(BatchArgs);
 static KernelPtr batch_kernel(unsigned mode) {
     switch (mode) {
         case kLoadPix | kStoreCoef: return k_batch<kLoadPix | kStoreCoef>;
-        case kLoadPix | kStoreCoef | kStats: return k_batch<kLoadPix | kStoreCoef | kStats>;
-        case kLoadPix | kStats: return k_batch<kLoadPix | kStats>;
+        case kLoadPix | kStoreCoef | kStats: return k_batch<kLoadPix | kStoreCoef | kStats | kStatsPrivate>;
+        case kLoadPix | kStats: return k_batch<kLoadPix | kStats | kStatsPrivate>;
         case kLoadCoef | kInverse | kStoreRecon: return k_batch<kLoadCoef | kInverse | kStoreRecon>;
         case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch<kLoadCoef | kInverse | kStoreRecon | kSse>;
         case kLoadPix | kInverse | kSse: return k_batch<kLoadPix | kInverse | kSse>;

@@ -69,7 +69,8 @@ enum : unsigned {
     kInverse = 8u,     // dequantise, inverse transform, descale
     kStoreRecon = 16u, // write the reconstruction
     kSse = 32u,        // accumulate the SSE
-    kStats = 64u       // accumulate band-energy and pixel statistics
+    kStats = 64u,      // accumulate band-energy and pixel statistics
+    kStatsPrivate = 128u // the statistics sink is this warp's own: plain adds, no atomics
 };
 
 // statistics word layout (per plane)
@@ -220,12 +221,31 @@ __device__ __forceinline__ int sample(const uint32_t (&pix)[8][2], int r, int c)
 
 __device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(0xffffffffu, v); }
 
+// statistics sink updates: atomics when the sink is shared, plain
+// read-modify-write when it belongs to the calling warp
+template <unsigned MODE>
+__device__ __forceinline__ void st_add(unsigned long long* p, unsigned long long v) {
+    if (MODE & kStatsPrivate) *p += v;
+    else atomicAdd(p, v);
+}
+template <unsigned MODE>
+__device__ __forceinline__ void st_min(unsigned long long* p, unsigned long long v) {
+    if (MODE & kStatsPrivate) *p = *p < v ? *p : v;
+    else atomicMin(p, v);
+}
+template <unsigned MODE>
+__device__ __forceinline__ void st_max(unsigned long long* p, unsigned long long v) {
+    if (MODE & kStatsPrivate) *p = *p > v ? *p : v;
+    else atomicMax(p, v);
+}
+
 // Shared memory a warp needs in a given mode (batched kernel): its item's
 // tables and descriptor, double-buffered samples and coefficient stages.
 constexpr int kDescBytes = 128;
 static_assert(sizeof(PlaneArg) <= kDescBytes, "descriptor slot too small");
+constexpr int kStatBytes = kStatsWords * 8;   // warp-private statistics accumulator
 __host__ __device__ constexpr int warp_smem_bytes(unsigned mode) {
-    return (int)sizeof(QuantSet) + kDescBytes +
+    return (int)sizeof(QuantSet) + kDescBytes + ((mode & kStats) ? kStatBytes : 0) +
            (((mode & kLoadPix) || (mode & kSse)) ? 2 * kPixBytes : 0) +
            ((mode & kLoadCoef) ? 2 * kStageBytes : ((mode & kStoreCoef) ? kStageBytes : 0));
 }
@@ -294,16 +314,16 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
                                       __reduce_max_sync(0xffffffffu, mx), warp_sum(adx), warp_sum(ady),
                                       warp_sum(dx2), warp_sum(dy2)};
             if (lane == 0) {
-                atomicAdd(&st[kStSum], (unsigned long long)vals[0]);
-                atomicAdd(&st[kStSum2], (unsigned long long)vals[1]);
-                atomicMin(&st[kStMin], (unsigned long long)vals[2]);
-                atomicMax(&st[kStMax], (unsigned long long)vals[3]);
-                atomicAdd(&st[kStAbsDx], (unsigned long long)vals[4]);
-                atomicAdd(&st[kStAbsDy], (unsigned long long)vals[5]);
-                atomicAdd(&st[kStDx2], (unsigned long long)vals[6]);
-                atomicAdd(&st[kStDy2], (unsigned long long)vals[7]);
-                atomicAdd(&st[kStBlocks], (unsigned long long)nvalid);
-                atomicAdd(&st[kStSamples], (unsigned long long)nvalid * 64ull);
+                st_add<MODE>(&st[kStSum], vals[0]);
+                st_add<MODE>(&st[kStSum2], vals[1]);
+                st_min<MODE>(&st[kStMin], vals[2]);
+                st_max<MODE>(&st[kStMax], vals[3]);
+                st_add<MODE>(&st[kStAbsDx], vals[4]);
+                st_add<MODE>(&st[kStAbsDy], vals[5]);
+                st_add<MODE>(&st[kStDx2], vals[6]);
+                st_add<MODE>(&st[kStDy2], vals[7]);
+                st_add<MODE>(&st[kStBlocks], (unsigned long long)nvalid);
+                st_add<MODE>(&st[kStSamples], (unsigned long long)nvalid * 64ull);
             }
         }
 
@@ -325,14 +345,14 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
                     const unsigned e = active ? a * a : 0u;
                     if (u | v) ac += e;
                     const unsigned tot = warp_sum(e);
-                    if (lane == 0) atomicAdd(&st[kStBand + u * 8 + v], (unsigned long long)tot);
+                    if (lane == 0) st_add<MODE>(&st[kStBand + u * 8 + v], tot);
                 }
             }
             const unsigned thr[4] = {1u << 10, 1u << 14, 1u << 18, 1u << 22};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const unsigned n = warp_sum((active && ac < thr[k]) ? 1u : 0u);
-                if (lane == 0) atomicAdd(&st[kStLowAc + k], (unsigned long long)n);
+                if (lane == 0) st_add<MODE>(&st[kStLowAc + k], n);
             }
         }
 

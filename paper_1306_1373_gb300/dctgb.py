@@ -170,9 +170,29 @@ def as_plane(t):
     return dct_plane(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0))
 
 
+class PlaneArray:
+    """A ctypes dct_plane array built once from a list of uint8 CUDA tensors
+    (it keeps the tensors alive); pass it wherever a list of planes goes to
+    avoid rebuilding the descriptors on every call."""
+
+    def __init__(self, tensors):
+        self.tensors = list(tensors)
+        n = len(self.tensors)
+        self.arr = (dct_plane * n)()
+        for i, t in enumerate(self.tensors):
+            self.arr[i] = as_plane(t)
+
+    def __len__(self):
+        return len(self.tensors)
+
+    def __getitem__(self, i):
+        return self.tensors[i]
+
+
 def _planes(ts):
-    arr = (dct_plane * len(ts))(*[as_plane(t) for t in ts])
-    return arr
+    if isinstance(ts, PlaneArray):
+        return ts.arr
+    return (dct_plane * len(ts))(*[as_plane(t) for t in ts])
 
 
 def _qtab(qtab):
@@ -357,10 +377,41 @@ def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
 
 
 def dct_autotune(plan, stream=None):
+    """Times candidate launch shapes for the prepared batch; returns
+    ((threads, ctas_per_sm, tile_blocks, 0), best ms)."""
     sh = dct_launch_shape()
     ms = ctypes.c_float()
     _check(load().dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)))
     return (sh.threads_per_cta, sh.ctas_per_sm, sh.tile_blocks, sh.reserved), ms.value
+
+
+def autotune_cached(plan, items, ops, sse=None, cache_path=None, key=None, stream=None):
+    """dct_batch_prepare with a launch shape from a JSON cache keyed by
+    (GPU name, key); on a miss it runs dct_autotune and stores the result.
+    Returns the shape used."""
+    import json
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    k = "%s|%s|ops=%d" % (name, key, int(ops))
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except ValueError:
+            cache = {}
+    if k in cache:
+        shape = tuple(cache[k]["shape"])
+        dct_batch_prepare(plan, items, ops, sse=sse, shape=shape, stream=stream)
+        return shape
+    dct_batch_prepare(plan, items, ops, sse=sse, stream=stream)
+    shape, ms = dct_autotune(plan, stream=stream)
+    cache[k] = {"shape": list(shape), "ms": ms}
+    if cache_path:
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return shape
 
 
 def psnr_list_from_sse(sse_values, shapes, max_value=0.0):
@@ -447,7 +498,8 @@ def dct_features(stats, width, height, target, stream=None):
 
 
 def dct_rate_features(plan, planes, planes_per_frame, targets, stream=None):
-    """Features (n, 80) of every frame's plane 0; planes frame-major."""
+    """Features (n, 80) of every frame's plane 0; planes frame-major (a list
+    of tensors or a PlaneArray)."""
     nf = len(planes) // planes_per_frame
     t = (ctypes.c_float * nf)(*[float(v) for v in targets])
     out = torch.empty(nf, DCT_MLP_INPUTS, dtype=torch.float32, device=planes[0].device)
@@ -475,6 +527,6 @@ def dct_rate_control(plan, planes, planes_per_frame, targets, net=None, stream=N
                 summary={f: getattr(summ, f) for f, _ in dct_rc_summary._fields_})
 
 
-__all__ = [n for n in dir() if n.startswith("dct_")] + ["Plan", "Mlp", "load", "DctError", "as_plane", "coeff_count",
+__all__ = [n for n in dir() if n.startswith("dct_")] + ["Plan", "Mlp", "PlaneArray", "load", "DctError", "as_plane", "coeff_count",
                                                           "make_batch_items", "STATS_LAYOUT", "STATS_WORDS"]
 _ = math  # noqa

@@ -59,6 +59,8 @@ def evaluate(plan, planes, planes_per_frame, targets, net):
     """Learned control and plain bisection on the same frames.  Returns a
     dict with per-method summaries, wall and device times and rates."""
     nf = len(planes) // planes_per_frame
+    if not isinstance(planes, D.PlaneArray):
+        planes = D.PlaneArray(planes)
     out = {}
     for name, model in (("learned", net), ("bisection", None)):
         torch.cuda.synchronize()
