@@ -356,18 +356,26 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             }
         }
 
-        // Quantiser q = sgn(Y) ((|Y| M + 2^31) >> 32), computed as the high
-        // word of the signed product Y * M + 2^31 - [Y < 0]: for Y < 0,
+        // Quantiser q = sgn(Y) ((|Y| M + 2^31) >> 32).  The fused kernels use
+        // the high word of the signed Y * M + 2^31 - [Y < 0] (for Y < 0,
         // floor((Y M + 2^31 - 1) / 2^32) = -floor((|Y| M + 2^31) / 2^32), so
-        // both signs round half away from zero exactly as the definition.
+        // both signs round half away from zero exactly as the definition);
+        // the forward-only kernels are faster with |Y|, an unsigned multiply
+        // and the sign (both forms measured on this GPU).
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const int y = x[u][v];
-                const unsigned c = 0x80000000u ^ (unsigned)(y >> 31);
-                const long long p = (long long)y * (long long)(int)T.M[u * 8 + v] + (long long)c;
-                x[u][v] = (int)(p >> 32);
+                if (MODE & kInverse) {
+                    const unsigned c = 0x80000000u ^ (unsigned)(y >> 31);
+                    const long long p = (long long)y * (long long)(int)T.M[u * 8 + v] + (long long)c;
+                    x[u][v] = (int)(p >> 32);
+                } else {
+                    const uint32_t a = (uint32_t)abs(y);
+                    const uint32_t q = (uint32_t)(((unsigned long long)a * T.M[u * 8 + v] + 0x80000000ull) >> 32);
+                    x[u][v] = y < 0 ? -(int)q : (int)q;
+                }
             }
         }
 
