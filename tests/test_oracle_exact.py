@@ -89,3 +89,34 @@ def test_exact_pipeline_quantiser_rounding():
         if abs(ratio - math.floor(ratio) - 0.5) > 1e-6:     # FP64 noise decides exact ties
             assert q[0, 0, 0] == int(math.copysign(math.floor(ratio + 0.5), x00))
         assert np.abs(q[0]).sum() == abs(q[0, 0, 0])
+
+
+def test_fp32_pipeline_matches_fp64_definition():
+    """The float32 exact pipeline (fixed operation order, as the GPU runs
+    it) against the FP64 definition of Eq. 6: identical codes except where
+    |X|/Q sits within float32 rounding of a .5 tie, reconstructions within 1,
+    PSNR within 0.01 dB."""
+    from oracle import exact_fp32
+    rng = np.random.default_rng(12)
+    b = rng.integers(0, 256, size=(3000, 8, 8)).astype(np.uint8)
+    for quality in (10, 50, 90, 100):
+        Q = ijg.luma_table(quality)
+        q64 = exact_dct.exact_compress_blocks(b, Q)
+        q32 = exact_fp32.compress_blocks(b, Q).astype(np.int64)
+        X = exact_dct.dct2(b.astype(np.float64) - 128.0)
+        frac = np.abs(X) / Q - np.floor(np.abs(X) / Q)
+        near_tie = np.abs(frac - 0.5) < 1e-4
+        assert np.array_equal(q32[~near_tie], q64[~near_tie])
+        assert np.abs(q32 - q64).max() <= 1
+        r64 = exact_dct.exact_reconstruct_blocks(q64, Q)
+        r32 = exact_fp32.reconstruct_blocks(q64, Q)
+        assert np.abs(r32.astype(int) - r64.astype(int)).max() <= 1
+        assert abs(psnr.psnr(b, r32) - psnr.psnr(b, r64)) < 0.01
+
+
+def test_fp32_pipeline_constant_blocks():
+    from oracle import exact_fp32
+    b = np.arange(256, dtype=np.uint8).reshape(256, 1, 1) * np.ones((1, 8, 8), dtype=np.uint8)
+    Q = ijg.luma_table(100)
+    r = exact_fp32.reconstruct_blocks(exact_fp32.compress_blocks(b, Q), Q)
+    assert np.abs(r.astype(int) - b.astype(int)).max() <= 1
