@@ -156,6 +156,17 @@ dct_status dct_codec_fused(dct_plan_t plan, const dct_plane* planes, int nplanes
                            const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
                            const dct_plane* recon_planes, uint64_t* sse_out, dct_stream_t stream);
 
+/* Exact-DCT pipeline: the "DCT" rows of Tables 3 and 4 (the orthonormal 2-D
+ * DCT of Eq. 6, quantiser, dequantiser, inverse), for comparing its PSNR with
+ * the Cordic-based path.  Computed in float32 with a fixed operation order
+ * (each product and sum rounded on its own, k ascending; q = sgn(X)
+ * floor(|X| / Q + 0.5); pixel = clamp(floor((y + 128) + 0.5), 0, 255)) so
+ * the codes are reproducible.  Arguments as dct_codec_fused; coeffs holds the
+ * exact pipeline's int16 codes. */
+dct_status dct_exact_fused(dct_plan_t plan, const dct_plane* planes, int nplanes, int quality,
+                           const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
+                           const dct_plane* recon_planes, uint64_t* sse_out, dct_stream_t stream);
+
 /* SSE and PSNR of two sets of planes of equal sizes (Eq. 23, Eq. 24).
  *  sse_out    device uint64[nplanes], overwritten.
  *  psnr_host  optional host double[nplanes + 1]: per-plane PSNR and the

@@ -93,6 +93,8 @@ _SIGNATURES = {
                                        ctypes.c_int, ctypes.POINTER(dct_plane), _P, _P]),
     "dct_codec_fused": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int, _U16P,
                                        ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
+    "dct_exact_fused": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int, _U16P,
+                                       ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
     "dct_psnr": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), ctypes.c_int, _P,
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "dct_psnr_from_sse": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]),
@@ -315,6 +317,19 @@ def dct_codec_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
     _require_cuda(sse, coeffs)
     qa, n = _qtab(qtab)
     _check(load().dct_codec_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
+                                  ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
+                                  _planes(recon_planes) if recon_planes is not None else None,
+                                  ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
+    return sse
+
+
+def dct_exact_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=None, sse=None, stream=None):
+    """Exact-DCT pipeline (float32, Eq. 6) in one pass; returns the per-plane
+    SSE tensor (int64)."""
+    if sse is None:
+        sse = torch.empty(len(planes), dtype=torch.int64, device=planes[0].device)
+    qa, n = _qtab(qtab)
+    _check(load().dct_exact_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                   ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                                   _planes(recon_planes) if recon_planes is not None else None,
                                   ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
