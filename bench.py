@@ -114,12 +114,15 @@ def algorithmic_ops_per_sample():
     return 2 + 2 * per_pass + 5 + 4 + 2 * per_pass + 5 + 3
 
 
+KERNEL_SOURCES = ("batch.cu", "kernels.cuh", "cordic_loeffler.cuh", "dctgb_spec.h")
+
+
 def kernel_sources_sha():
+    """Hash of the files that define the batched kernels (the dominant kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_1373_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -253,6 +256,70 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     _ = torch
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# context: Tables 1-4 of the paper on this GPU
+# ---------------------------------------------------------------------------
+
+# Tables 1 and 2: image sizes and the paper's GTX 480 / i3-2130 times (ms)
+PAPER_SIZES = [("Lena", 3072, 3072, 1020.32, 8.92), ("Lena", 2048, 2048, 266.23, 5.61),
+               ("Lena", 1600, 1400, 116.12, 2.20), ("Lena", 1024, 814, 88.23, 1.24),
+               ("Lena", 576, 720, 48.52, 0.82), ("Lena", 512, 512, 16.42, 0.62), ("Lena", 200, 200, 6.88, 0.24),
+               ("Cable-car", 544, 512, 30.32, 0.58), ("Cable-car", 512, 480, 26.84, 0.41),
+               ("Cable-car", 448, 416, 21.22, 0.34), ("Cable-car", 384, 352, 17.28, 0.26),
+               ("Cable-car", 320, 288, 10.86, 0.19)]
+
+
+def exact_vs_cordic(D, planes, chroma):
+    """PSNR of the exact float32 DCT pipeline and of the Cordic-based one on
+    the benchmark planes (the comparison of Tables 3 and 4)."""
+    import torch
+    out = {}
+    names = ["grey", "Y", "Cb", "Cr"]
+    with D.Plan(8192, 8192) as pg, D.Plan(8192, 8192, layout=D.DCT_LAYOUT_YUV420) as py:
+        for plan, idx in ((pg, [0]), (py, [1, 2, 3])):
+            ps = [planes[i] for i in idx]
+            se = D.dct_exact_fused(plan, ps, QUALITY).cpu().tolist()
+            sc = D.dct_codec_fused(plan, ps, QUALITY).cpu().tolist()
+            for k, i in enumerate(idx):
+                n = planes[i].numel()
+                out[names[i]] = {"exact_db": D.dct_psnr_from_sse(se[k], n), "cordic_db": D.dct_psnr_from_sse(sc[k], n)}
+    torch.cuda.synchronize()
+    return out
+
+
+def paper_size_sweep(D, dev, reps=50):
+    """GPU time of one compress + reconstruct + PSNR pass per image at the
+    paper's sizes (1/f^2 noise stand-ins, quality 75), as a one-item batch
+    replayed from its CUDA graph, next to the paper's own times (GTX 480 and
+    i3-2130, context only)."""
+    import torch
+    from synth import powerlaw_image
+    out = []
+    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    with D.Plan(3072, 3072, max_batch=1) as plan:
+        for name, w, h, cpu_ms, gpu_ms in PAPER_SIZES:
+            img = powerlaw_image(h, w, seed=w * 7 + h, device=dev)
+            coef = torch.empty(D.coeff_count([img.shape]), dtype=torch.int16, device=dev)
+            rec = torch.empty_like(img)
+            sse = torch.zeros(1, dtype=torch.int64, device=dev)
+            D.dct_batch_prepare(plan, D.make_batch_items([img], [QUALITY], coeffs=[coef], recons=[rec]), C | R | S,
+                                sse=sse, shape=(256, 8, 32, 0))
+            for _ in range(3):
+                D.dct_batch_launch(plan)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                D.dct_batch_launch(plan)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out.append({"image": "%s %dx%d" % (name, w, h), "gb300_ms": ms,
+                        "gb300_mpix_s": w * h / (ms * 1e-3) / 1e6, "paper_gtx480_ms": gpu_ms,
+                        "paper_i3_ms": cpu_ms, "psnr_db": D.dct_psnr_from_sse(int(sse[0]), w * h)})
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -523,6 +590,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(planes[0].cpu().numpy(), args.cpu_seconds)
     plan.close()
+    line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
+    line["paper_sizes"] = paper_size_sweep(D, dev)
     if not args.no_ratecontrol:
         del planes, coefs, recons, flush
         torch.cuda.empty_cache()
