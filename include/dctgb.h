@@ -167,6 +167,17 @@ dct_status dct_exact_fused(dct_plan_t plan, const dct_plane* planes, int nplanes
                            const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
                            const dct_plane* recon_planes, uint64_t* sse_out, dct_stream_t stream);
 
+/* RGB to YCbCr 4:2:0 (no counterpart in the paper, which works on grey
+ * images): full-range BT.601 as in JFIF with 16-bit fixed-point coefficients
+ * (Y = (19595 R + 38470 G + 7471 B + 32768) >> 16, Cb and Cr likewise with
+ * offset 128 and clamping), chroma averaged over 2x2 as (a+b+c+d+2) >> 2 with
+ * the edge pixel repeated for odd sizes.
+ *  rgb        device, interleaved R,G,B bytes, rgb_pitch bytes between rows
+ *  y          width x height output plane (device data written)
+ *  cb, cr     ceil(width/2) x ceil(height/2) output planes */
+dct_status dct_rgb_to_yuv420(const uint8_t* rgb, int32_t width, int32_t height, int32_t rgb_pitch,
+                             const dct_plane* y, const dct_plane* cb, const dct_plane* cr, dct_stream_t stream);
+
 /* SSE and PSNR of two sets of planes of equal sizes (Eq. 23, Eq. 24).
  *  sse_out    device uint64[nplanes], overwritten.
  *  psnr_host  optional host double[nplanes + 1]: per-plane PSNR and the

@@ -95,6 +95,8 @@ _SIGNATURES = {
                                        ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
     "dct_exact_fused": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int, _U16P,
                                        ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
+    "dct_rgb_to_yuv420": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(dct_plane),
+                                         ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), _P]),
     "dct_psnr": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), ctypes.c_int, _P,
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "dct_psnr_from_sse": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]),
@@ -334,6 +336,22 @@ def dct_exact_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
                                   _planes(recon_planes) if recon_planes is not None else None,
                                   ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
     return sse
+
+
+def dct_rgb_to_yuv420(rgb, y=None, cb=None, cr=None, stream=None):
+    """(H, W, 3) uint8 CUDA tensor (rows may be padded) -> (Y, Cb, Cr) planes."""
+    if rgb.dtype != torch.uint8 or rgb.dim() != 3 or rgb.shape[2] != 3 or rgb.stride(2) != 1 or rgb.stride(1) != 3:
+        raise ValueError("rgb must be an (H, W, 3) uint8 tensor with interleaved channels")
+    _require_cuda(rgb)
+    h, w = rgb.shape[:2]
+    ch, cw = (h + 1) // 2, (w + 1) // 2
+    y = torch.empty(h, w, dtype=torch.uint8, device=rgb.device) if y is None else y
+    cb = torch.empty(ch, cw, dtype=torch.uint8, device=rgb.device) if cb is None else cb
+    cr = torch.empty(ch, cw, dtype=torch.uint8, device=rgb.device) if cr is None else cr
+    py, pb, pr = as_plane(y), as_plane(cb), as_plane(cr)
+    _check(load().dct_rgb_to_yuv420(ctypes.c_void_p(rgb.data_ptr()), w, h, rgb.stride(0), ctypes.byref(py),
+                                    ctypes.byref(pb), ctypes.byref(pr), _stream_ptr(stream)))
+    return y, cb, cr
 
 
 def dct_psnr(plan, a_planes, b_planes, max_value=0.0, sse=None, host=True, stream=None):
