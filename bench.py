@@ -289,6 +289,19 @@ def exact_vs_cordic(D, planes, chroma):
     return out
 
 
+def rate_of_coefficients(D, coefs, shapes):
+    """Bits per sample of the benchmark planes' coefficients (JPEG-style
+    symbols at their ideal static code length) and the implied ratio."""
+    out = {}
+    names = ["grey", "Y", "Cb", "Cr"]
+    with D.Plan(8192, 8192) as plan:
+        for name, c, sh in zip(names, coefs, shapes):
+            st = D.dct_entropy_stats(plan, c, [sh]).cpu().numpy()[0]
+            bps = D.dct_entropy_bits(st) / (sh[0] * sh[1])
+            out[name] = {"bits_per_sample": bps, "ratio": 8.0 / bps}
+    return out
+
+
 def paper_size_sweep(D, dev, reps=50):
     """GPU time of one compress + reconstruct + PSNR pass per image at the
     paper's sizes (1/f^2 noise stand-ins, quality 75), as a one-item batch
@@ -591,6 +604,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(planes[0].cpu().numpy(), args.cpu_seconds)
     plan.close()
     line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
+    line["rate"] = rate_of_coefficients(D, coefs, shapes)
     line["paper_sizes"] = paper_size_sweep(D, dev)
     if not args.no_ratecontrol:
         del planes, coefs, recons, flush

@@ -178,6 +178,24 @@ dct_status dct_exact_fused(dct_plan_t plan, const dct_plane* planes, int nplanes
 dct_status dct_rgb_to_yuv420(const uint8_t* rgb, int32_t width, int32_t height, int32_t rgb_pitch,
                              const dct_plane* y, const dct_plane* cb, const dct_plane* cr, dct_stream_t stream);
 
+/* Rate of quantised coefficients (no counterpart in the paper, which never
+ * measures the compressed size): counts of the JPEG-style symbols of each
+ * plane.  Per plane DCT_ENTROPY_WORDS uint64 words (device, overwritten):
+ * 0..15 DC categories of the block-major DC differences (first block
+ * predicted by 0), 16..271 AC run/size symbols in zig-zag order (ZRL 0xF0
+ * per 16 zeros before a value, EOB 0x00 for trailing zeros), 272 amplitude
+ * bits, 273 blocks.  coeffs is laid out as dct_compress writes it for
+ * planes of the given sizes (only width and height are read).
+ * Synchronises `stream` before launching (host block counts are uploaded). */
+#define DCT_ENTROPY_WORDS 274
+dct_status dct_entropy_stats(dct_plan_t plan, const int16_t* coeffs, const dct_plane* planes, int nplanes,
+                             uint64_t* stats_out, dct_stream_t stream);
+
+/* Host only: bits of one plane from its DCT_ENTROPY_WORDS words: amplitude
+ * bits + sum over the DC and the AC counts of n log2(N / n) (the length of an
+ * ideal static code for the plane's own symbol statistics). */
+double dct_entropy_bits(const uint64_t* stats_host);
+
 /* SSE and PSNR of two sets of planes of equal sizes (Eq. 23, Eq. 24).
  *  sse_out    device uint64[nplanes], overwritten.
  *  psnr_host  optional host double[nplanes + 1]: per-plane PSNR and the

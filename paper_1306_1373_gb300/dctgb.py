@@ -97,6 +97,8 @@ _SIGNATURES = {
                                        ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
     "dct_rgb_to_yuv420": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(dct_plane),
                                          ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), _P]),
+    "dct_entropy_stats": (ctypes.c_int, [_P, _P, ctypes.POINTER(dct_plane), ctypes.c_int, _P, _P]),
+    "dct_entropy_bits": (ctypes.c_double, [ctypes.POINTER(ctypes.c_uint64)]),
     "dct_psnr": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), ctypes.c_int, _P,
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "dct_psnr_from_sse": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]),
@@ -352,6 +354,26 @@ def dct_rgb_to_yuv420(rgb, y=None, cb=None, cr=None, stream=None):
     _check(load().dct_rgb_to_yuv420(ctypes.c_void_p(rgb.data_ptr()), w, h, rgb.stride(0), ctypes.byref(py),
                                     ctypes.byref(pb), ctypes.byref(pr), _stream_ptr(stream)))
     return y, cb, cr
+
+
+DCT_ENTROPY_WORDS = 274
+
+
+def dct_entropy_stats(plan, coeffs, shapes, stream=None):
+    """Symbol statistics (device int64 tensor, planes x 274) of coefficients
+    laid out for planes of the given (height, width) shapes."""
+    n = len(shapes)
+    arr = (dct_plane * n)(*[dct_plane(None, w, h, w) for h, w in shapes])
+    out = torch.empty(n, DCT_ENTROPY_WORDS, dtype=torch.int64, device=coeffs.device)
+    _check(load().dct_entropy_stats(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), arr, n,
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def dct_entropy_bits(stats_row):
+    """Bits of one plane from its 274 statistics words (host)."""
+    a = np.ascontiguousarray(np.asarray(stats_row, dtype=np.uint64))
+    return load().dct_entropy_bits(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
 
 
 def dct_psnr(plan, a_planes, b_planes, max_value=0.0, sse=None, host=True, stream=None):
