@@ -15,10 +15,6 @@
 
 #include "host_common.h"
 
-#ifndef DCTGB_PREFETCH
-#define DCTGB_PREFETCH 1    // cp.async prefetch of the next tile in the batched kernel
-#endif
-
 namespace dctgb {
 
 struct BatchArgs {
@@ -109,7 +105,7 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
             __syncwarp();
             pf_valid = false;
         }
-        const bool next_same = DCTGB_PREFETCH && tile + 1 < t_end && tile + 1 < item_end;
+        const bool next_same = tile + 1 < t_end && tile + 1 < item_end;
         if (next_same) {
             const int nt = tile + 1 - P.tile_begin;
             if (kPixPf) {

@@ -20,24 +20,14 @@
 #pragma once
 #include "dctgb_spec.h"
 
-#ifndef DCTGB_MADHI
-#define DCTGB_MADHI 0
-#endif
 
 namespace dctgb {
 
-// acc + (v >> I) with an arithmetic (floor) shift.  With DCTGB_MADHI and
-// I >= 2 it is one mad.hi.s32: the high word of v * 2^(32-I) is exactly
-// floor(v / 2^I), added to acc in the same instruction.
+// acc + (v >> I) with an arithmetic (floor) shift.  (A single mad.hi.s32
+// computes the same value, but it issues at half rate on this GPU and
+// measured no faster than the shift and add.)
 template <int I>
 __device__ __forceinline__ int add_shr(int acc, int v) {
-#if DCTGB_MADHI
-    if constexpr (I >= 2) {
-        int d;
-        asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(v), "n"(1 << (32 - I)), "r"(acc));
-        return d;
-    }
-#endif
     return acc + (v >> I);
 }
 
