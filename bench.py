@@ -11,7 +11,7 @@ Also measures learned rate control against plain 8-step bisection on the
 20,000-image grey set and the 2,000-frame 4:2:0 stream ("ratecontrol").
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
-(the reference arm of this build) on bounded samples of the same workload.
+(the reference arm) on bounded samples of the same workload.
 Multi-GPU: replicas only (every rank runs the same workload independently,
 no collective on the data path); value = samples of all ranks / max time.
 """
