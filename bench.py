@@ -549,10 +549,41 @@ def main():
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
         ok = bool(torch.equal(sets[0]["hsse"], sets[1]["hsse"])) and sets[0]["hsse"].tolist() == sse_h
+
+        # The host link alone: the same copies, both directions at once, with
+        # no codec between them.  e2e cannot beat this time per step.
+        def link_only(k):
+            st = sets[k & 1]
+            with torch.cuda.stream(s_in):
+                for hp, dp in zip(host_in, st["din"]):
+                    dp.copy_(hp, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                for hc, dc in zip(st["hco"], st["dco"]):
+                    hc.copy_(dc, non_blocking=True)
+                st["hsse"].copy_(st["dsse"], non_blocking=True)
+
+        link_only(0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s_ in (s_in, s_out):
+            s_.wait_event(e0)
+        for k in range(e2e_steps):
+            link_only(k)
+        for s_ in (s_in, s_out):
+            ev_ = torch.cuda.Event()
+            ev_.record(s_)
+            stream.wait_event(ev_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        link_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
         e2e = {"value": replica_throughput(samples, world, e2e_ms), "unit": "MPix/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "pipeline": "2 buffer sets, streams for copy-in / codec graph / copy-out",
-               "sse_matches_device_run": ok}
+               "sse_matches_device_run": ok,
+               "host_link": {"ms_per_step": link_ms, "frac": link_ms / e2e_ms,
+                             "h2d_gbs": h2d / link_ms / 1e6, "d2h_gbs": d2h / link_ms / 1e6,
+                             "note": "the same copies with no codec between them, both directions at once; "
+                                     "frac = link time / e2e time"}}
         sets[1]["plan"].close()
 
     # ---- roofline of the dominant kernel.  The path is bound by integer

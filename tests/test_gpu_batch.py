@@ -209,3 +209,51 @@ def test_batch_invalid_arguments(D):
     with D.Plan(32, 32, max_batch=0) as plan:
         with pytest.raises(D.DctError):
             D.dct_batch_prepare(plan, D.make_batch_items([t], [50], coeffs=[c]), D.DCT_OP_COMPRESS)
+
+
+def test_batch_maximum_plane_sampled(D):
+    """The largest plane a plan accepts below 2^31 samples, 32767 x 65535
+    (ragged in both directions), through the fused batch in the benchmark's
+    launch shape: the last block row and column and 1024 random interior
+    blocks against the oracle, the SSE against the reconstruction."""
+    h, w = 32767, 65535
+    quality = 50
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(65535)
+    src = torch.randint(0, 256, (h, w), dtype=torch.uint8, device="cuda", generator=gen)
+    nby, nbx = (h + 7) // 8, (w + 7) // 8
+    with D.Plan(w, h, max_batch=1) as plan:
+        coef = torch.empty(D.coeff_count([src.shape]), dtype=torch.int16, device="cuda")
+        rec = torch.empty_like(src)
+        sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+        arr = D.make_batch_items([src], [quality], coeffs=[coef], recons=[rec])
+        D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS | D.DCT_OP_RECONSTRUCT | D.DCT_OP_SSE, sse=sse,
+                            shape=(256, 16, 32, 0))
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+    Q = ijg.luma_table(quality)
+    cblk = coef.view(nby, nbx, 8, 8)
+    # last block row and last block column: oracle on the edge strips
+    for strip, rstrip, idx in ((src[8 * (nby - 1):, :], rec[8 * (nby - 1):, :], (slice(nby - 1, nby), slice(None))),
+                               (src[:, 8 * (nbx - 1):], rec[:, 8 * (nbx - 1):], (slice(None), slice(nbx - 1, nbx)))):
+        img = strip.cpu().numpy()
+        c_or = codec.compress_plane(img, Q)
+        assert np.array_equal(cblk[idx].cpu().numpy(), c_or)
+        assert np.array_equal(rstrip.cpu().numpy(), codec.reconstruct_plane(c_or, Q, *img.shape))
+    # random interior blocks
+    rng = np.random.default_rng(3)
+    by = torch.from_numpy(rng.integers(0, nby - 1, 1024)).cuda()
+    bx = torch.from_numpy(rng.integers(0, nbx - 1, 1024)).cuda()
+    r8 = torch.arange(8, device="cuda")
+    rows = (8 * by[:, None] + r8)[:, :, None]
+    cols = (8 * bx[:, None] + r8)[:, None, :]
+    blocks = src[rows, cols].cpu().numpy()
+    c_or = codec.compress_blocks(blocks, Q)
+    assert np.array_equal(cblk[by, bx].cpu().numpy(), c_or)
+    assert np.array_equal(rec[rows, cols].cpu().numpy(), codec.reconstruct_blocks(c_or, Q))
+    # SSE of the whole plane, in row chunks
+    tot = 0
+    for r0 in range(0, h, 4096):
+        d = rec[r0:r0 + 4096].to(torch.int32) - src[r0:r0 + 4096].to(torch.int32)
+        tot += int((d * d).sum(dtype=torch.int64))
+    assert int(sse[0]) == tot
