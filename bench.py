@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--shape", default=None, help="threads,ctas_per_sm: fixed launch shape, no autotuning")
+    ap.add_argument("--shape", default=None,
+                    help="threads,ctas_per_sm[,lanes_per_block]: fixed launch shape, no autotuning")
     ap.add_argument("--no-ratecontrol", action="store_true", help="skip the learned-rate-control workloads")
     ap.add_argument("--rc-epochs", type=int, default=300)
     return ap.parse_args()
@@ -410,6 +411,44 @@ def paper_size_sweep(D, dev, reps=50):
     return out
 
 
+def batch512(D, dev, ops_per_sample, alu_peak_tops, hbm_gbs, reps=20):
+    """The batched workload of uneven images: 512 grey planes, W and H
+    multiples of 8 in [64, 2048], quality 10..95, 1/f^beta content with beta
+    in [1, 3]; one autotuned persistent launch replayed from its CUDA graph
+    (the inputs, about 0.57 GB, exceed the L2, so nothing is flushed)."""
+    import torch
+    from synth import batch_workload, powerlaw_image
+    spec = batch_workload(512)
+    srcs = [powerlaw_image(it["height"], it["width"], seed=it["seed"], beta=it["beta"], device=dev) for it in spec]
+    quals = [it["quality"] for it in spec]
+    samples = sum(int(s.numel()) for s in srcs)
+    coefs = [torch.empty(D.coeff_count([s.shape]), dtype=torch.int16, device=dev) for s in srcs]
+    recs = [torch.empty_like(s) for s in srcs]
+    sse = torch.zeros(len(srcs), dtype=torch.int64, device=dev)
+    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    with D.Plan(2048, 2048, max_batch=len(srcs)) as plan:
+        D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals, coeffs=coefs, recons=recs), C | R | S, sse=sse)
+        shape, _ = D.dct_autotune(plan)
+        for _ in range(3):
+            D.dct_batch_launch(plan)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        stream = torch.cuda.current_stream()
+        for k in range(reps):
+            ev[k][0].record(stream)
+            D.dct_batch_launch(plan)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+    sse_h = sse.cpu().tolist()
+    psnrs = [D.dct_psnr_from_sse(int(e), int(t.numel())) for e, t in zip(sse_h, srcs)]
+    gpix = samples / (ms * 1e-3) / 1e9
+    return {"workload": "512 grey images, W and H multiples of 8 in [64, 2048], quality 10..95, 1/f^beta, "
+                        "beta 1..3", "samples": samples, "ms": ms, "mpix_s": gpix * 1e3,
+            "shape": {"threads_per_cta": shape[0], "ctas_per_sm": shape[1], "lanes_per_block": max(1, shape[3])},
+            "alu_frac": gpix * ops_per_sample / 1e3 / alu_peak_tops, "hbm_frac": gpix * 4 / hbm_gbs,
+            "psnr_db_mean": sum(psnrs) / len(psnrs)}
+
+
 # ---------------------------------------------------------------------------
 # learned rate control vs bisection
 # ---------------------------------------------------------------------------
@@ -516,8 +555,8 @@ def main():
         ops |= D.DCT_OP_TWO_PASS
     items = D.make_batch_items(planes, [QUALITY] * len(planes), coeffs=coefs, recons=recons, chroma=chroma)
     if args.shape:
-        t, c = (int(v) for v in args.shape.split(","))
-        shape = (t, c, 32, 0)
+        f = [int(v) for v in args.shape.split(",")]
+        shape = (f[0], f[1], 32, f[2] if len(f) > 2 else 0)
         D.dct_batch_prepare(plan, items, ops, sse=sse, shape=shape)
     else:
         D.dct_batch_prepare(plan, items, ops, sse=sse)
@@ -698,6 +737,7 @@ def main():
             "config": {"workload": WORKLOAD, "samples_per_step": samples, "path": args.path,
                        "launch": "one graph: SSE clear + persistent batched kernel(s)",
                        "shape": {"threads_per_cta": shape[0], "ctas_per_sm": shape[1],
+                                 "lanes_per_block": max(1, shape[3]),
                                  "source": "fixed" if args.shape else "dct_autotune"},
                        "l2": "flushed between timed steps (inputs 79.6 MB < 129 MB L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -715,9 +755,10 @@ def main():
     line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
     line["rate"] = rate_of_coefficients(D, coefs, shapes)
     line["paper_sizes"] = paper_size_sweep(D, dev)
+    del planes, coefs, recons, flush
+    torch.cuda.empty_cache()
+    line["batch512"] = batch512(D, dev, roof["ops_per_sample"], roof["peak"], roof["hbm"]["peak"])
     if not args.no_ratecontrol:
-        del planes, coefs, recons, flush
-        torch.cuda.empty_cache()
         line["ratecontrol"] = {"grey": rc_grey(dev, args.rc_epochs), "stream420": rc_stream(dev, args.rc_epochs)}
     if rank == 0:
         print(json.dumps(line))

@@ -238,8 +238,10 @@ typedef struct {
 typedef struct {
     int32_t threads_per_cta;   /* 64..256, multiple of 32 */
     int32_t ctas_per_sm;       /* >= 1 */
-    int32_t tile_blocks;       /* 8x8 blocks per warp tile: 32 or 64 */
-    int32_t reserved;
+    int32_t tile_blocks;       /* 8x8 blocks per warp tile: 32 */
+    int32_t lanes_per_block;   /* 0 or 1: one lane per 8x8 block; 2: two lanes
+                                * per block (fused COMPRESS/RECONSTRUCT/SSE
+                                * operations only; other operations use one) */
 } dct_launch_shape;
 
 /* Uploads a work list of n items (1..max_batch) to the plan's workspace,

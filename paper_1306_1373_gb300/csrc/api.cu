@@ -84,6 +84,11 @@ dct_status build_tables(int quality, const uint16_t* qtab, int qtab_entries, int
             out.M[i] = (uint32_t)m;
             out.W[i] = (int32_t)w;
             out.QW[i] = q[i] * (int32_t)w;
+            // the kernels quantise the non-tie entries without the sign term,
+            // which is exact only while M has at most 11 trailing zero bits
+            // (tie_entry); every Q in 1..255 satisfies this
+            if (!tie_entry(u, v) && (out.M[i] & kTieFreeBits) == 0)
+                return fail(DCT_ERR_UNSUPPORTED, "quantiser multiplier outside the tie-free range");
         }
     }
     return DCT_OK;
@@ -192,7 +197,7 @@ dct_status dct_plan_create(dct_plan_t* out, const dct_plan_desc* desc, dct_strea
     p->shape.threads_per_cta = 256;
     p->shape.ctas_per_sm = 0;     // 0: use the occupancy-derived default
     p->shape.tile_blocks = kTileBlocks;
-    p->shape.reserved = 0;
+    p->shape.lanes_per_block = 0;
     p->batch = nullptr;
     p->rc = nullptr;
     *out = p;

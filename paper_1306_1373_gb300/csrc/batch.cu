@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "host_common.h"
+#include "kernels_pair.cuh"
 
 namespace dctgb {
 
@@ -135,6 +136,52 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
     }
 }
 
+// The fused modes with two lanes per 8x8 block (kernels_pair.cuh): the same
+// contiguous tile ranges and per-item descriptor/table slot as k_batch; the
+// samples are read straight from global memory (the 32 resident warps per SM
+// hide the latency that the one-lane kernel hides with cp.async prefetch).
+template <unsigned MODE>
+__global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __grid_constant__ BatchArgs args) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int kWarpBytes = pair_warp_smem_bytes();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int warps_per_cta = blockDim.x >> 5;
+    uint8_t* base = smem + (size_t)warp * kWarpBytes;
+    QuantSet* T = reinterpret_cast<QuantSet*>(base);
+    PlaneArg& P = *reinterpret_cast<PlaneArg*>(base + sizeof(QuantSet));
+    uint8_t* xb = base + sizeof(QuantSet) + kDescBytes;
+
+    const long long total_warps = (long long)gridDim.x * warps_per_cta;
+    const long long gw = (long long)blockIdx.x * warps_per_cta + warp;
+    const int t_begin = (int)((gw * args.ntiles) / total_warps);
+    const int t_end = (int)(((gw + 1) * args.ntiles) / total_warps);
+
+    int cur = -1;
+    int item_end = 0;
+    unsigned long long* item_sse = nullptr;
+    unsigned long long sse = 0ull;
+    for (int tile = t_begin; tile < t_end; ++tile) {
+        if (cur < 0 || tile >= item_end) {
+            __syncwarp();
+            if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
+            sse = 0ull;
+            cur = find_item(args.tile_begin, args.nitems, tile);
+            item_end = __ldg(args.tile_begin + cur + 1);
+            const PlaneArg* gi = args.items + cur;
+            item_sse = gi->sse;
+            if (lane < (int)(sizeof(PlaneArg) / 4))
+                reinterpret_cast<uint32_t*>(&P)[lane] = __ldg(reinterpret_cast<const uint32_t*>(gi) + lane);
+            const uint4* s = reinterpret_cast<const uint4*>(args.tabs + __ldg(&gi->table));
+            uint4* d = reinterpret_cast<uint4*>(T);
+            for (int i = lane; i < (int)(sizeof(QuantSet) / 16); i += 32) d[i] = __ldg(s + i);
+            __syncwarp();
+        }
+        sse += process_tile_pair<MODE>(P, *T, tile - P.tile_begin, lane, xb);
+    }
+    if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
+}
+
 // Clears the SSE words (and statistics, with min words set to all ones).
 __global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -152,7 +199,27 @@ __global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_s
 
 using KernelPtr = void (*)(BatchArgs);
 
-static KernelPtr batch_kernel(unsigned mode) {
+static KernelPtr pair_kernel(unsigned mode) {
+    switch (mode) {
+        case kLoadPix | kInverse | kSse: return k_batch_pair<kLoadPix | kInverse | kSse>;
+        case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef>;
+        case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreRecon>;
+        case kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon:
+            return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon>;
+        case kLoadPix | kInverse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kStoreRecon>;
+        case kLoadPix | kInverse | kStoreCoef | kStoreRecon:
+            return k_batch_pair<kLoadPix | kInverse | kStoreCoef | kStoreRecon>;
+        default: return nullptr;
+    }
+}
+
+// Two lanes per block when the shape asks for it and the mode has a two-lane
+// kernel; one lane per block otherwise.
+static bool use_pair(unsigned mode, const dct_launch_shape& sh) {
+    return sh.lanes_per_block == 2 && pair_kernel(mode) != nullptr;
+}
+
+static KernelPtr one_lane_kernel(unsigned mode) {
     switch (mode) {
         case kLoadPix | kStoreCoef: return k_batch<kLoadPix | kStoreCoef>;
         case kLoadPix | kStoreCoef | kStats: return k_batch<kLoadPix | kStoreCoef | kStats | kStatsPrivate>;
@@ -169,6 +236,10 @@ static KernelPtr batch_kernel(unsigned mode) {
             return k_batch<kLoadPix | kInverse | kStoreCoef | kStoreRecon>;
         default: return nullptr;
     }
+}
+
+static KernelPtr batch_kernel(unsigned mode, const dct_launch_shape& sh) {
+    return use_pair(mode, sh) ? pair_kernel(mode) : one_lane_kernel(mode);
 }
 
 struct BatchState {
@@ -230,14 +301,17 @@ static dct_status ensure_state(dct_plan_t plan) {
     return DCT_OK;
 }
 
-static size_t batch_smem(int threads, unsigned mode) { return (size_t)(threads / 32) * warp_smem_bytes(mode); }
+static size_t batch_smem(int threads, unsigned mode, const dct_launch_shape& sh) {
+    return (size_t)(threads / 32) * (use_pair(mode, sh) ? pair_warp_smem_bytes() : warp_smem_bytes(mode));
+}
 
 static int batch_grid(const dct_plan_s* plan, unsigned mode, const dct_launch_shape& sh, int ntiles) {
     const int threads = sh.threads_per_cta;
     int per_sm = sh.ctas_per_sm;
     if (per_sm <= 0) {
         int occ = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(mode), threads, batch_smem(threads, mode)) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(mode, sh), threads,
+                                                          batch_smem(threads, mode, sh)) !=
                 cudaSuccess || occ < 1)
             occ = 1;
         per_sm = occ;
@@ -268,8 +342,8 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     a.nitems = b->n;
     a.ntiles = b->ntiles;
     for (int k = 0; k < b->nkernels; ++k) {
-        KernelPtr kp = batch_kernel(b->modes[k]);
-        const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k]);
+        KernelPtr kp = batch_kernel(b->modes[k], sh);
+        const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k], sh);
         cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kp<<<batch_grid(plan, b->modes[k], sh, b->ntiles), sh.threads_per_cta, smem, s>>>(a);
     }
@@ -290,16 +364,17 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
 
 static bool valid_shape(const dct_launch_shape& sh) {
     return sh.threads_per_cta >= 64 && sh.threads_per_cta <= 256 && sh.threads_per_cta % 32 == 0 &&
-           sh.ctas_per_sm >= 0 && sh.ctas_per_sm <= 32 && sh.tile_blocks == kTileBlocks;
+           sh.ctas_per_sm >= 0 && sh.ctas_per_sm <= 32 && sh.tile_blocks == kTileBlocks &&
+           sh.lanes_per_block >= 0 && sh.lanes_per_block <= 2;
 }
 
 cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* tile_begin, const QuantSet* tabs,
                          int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s) {
-    KernelPtr kp = batch_kernel(mode);
-    if (!kp) return cudaErrorInvalidValue;
     dct_launch_shape sh = plan->shape;
     if (!valid_shape(sh)) sh = dct_launch_shape{256, 0, kTileBlocks, 0};
-    const size_t smem = batch_smem(sh.threads_per_cta, mode);
+    KernelPtr kp = batch_kernel(mode, sh);
+    if (!kp) return cudaErrorInvalidValue;
+    const size_t smem = batch_smem(sh.threads_per_cta, mode, sh);
     cudaError_t e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     BatchArgs a;
@@ -460,15 +535,21 @@ dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host,
     }
     // candidate shapes: CTA sizes x CTAs per SM (beyond the resident count the
     // grid is simply oversubscribed: more, shorter contiguous tile ranges)
+    // and, where the prepared operation has a two-lane kernel, both lanes
+    // per block
     const int threads_c[] = {64, 128, 256};
     const int per_sm_c[] = {1, 2, 4, 8, 16};
+    bool pair_ok = true;
+    for (int k = 0; k < plan->batch->nkernels; ++k) pair_ok = pair_ok && pair_kernel(plan->batch->modes[k]) != nullptr;
+    const int nlanes = pair_ok ? 2 : 1;
     dct_launch_shape best_sh = plan->batch->shape;
     float best_ms = 1e30f;
     dct_status st = DCT_OK;
+    for (int lanes = 1; lanes <= nlanes; ++lanes)
     for (int t : threads_c) {
         for (int c : per_sm_c) {
             if (t * c > 4096) continue;
-            dct_launch_shape sh{t, c, kTileBlocks, 0};
+            dct_launch_shape sh{t, c, kTileBlocks, lanes};
             if ((st = capture(plan, sh)) != DCT_OK) goto done;
             for (int w = 0; w < 2; ++w) cudaGraphLaunch(plan->batch->exec, s);
             float times[7];

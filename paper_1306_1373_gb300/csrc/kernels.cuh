@@ -73,6 +73,22 @@ enum : unsigned {
     kStatsPrivate = 128u // the statistics sink is this warp's own: plain adds, no atomics
 };
 
+// Quantiser entries that can meet an exact rounding tie.  The definition
+// q = sgn(Y) ((|Y| M + 2^31) >> 32) equals the high word of the signed
+// Y M + 2^31 for Y >= 0 always, and for Y < 0 unless |Y| M = 2^31 (mod 2^32),
+// which needs |Y| = 2^(31-k) * odd, k = trailing zero bits of M.  The forward
+// graph keeps |Y| <= 719380 < 2^20 (interval bound), so an entry with k <= 11
+// never ties.  Where u and v are both 0 or 4, g_u g_v = 1 and
+// M = rint(2^25 / Q) is a high power of two for Q = 1, 2, 4, ...: these four
+// entries keep the sign-aware form.  For the other 60, every Q in 1..255
+// gives k <= 11 (build_tables checks each table), so the plain high word is
+// the exact quantiser there: one 64-bit multiply-add per coefficient.
+__host__ __device__ constexpr bool tie_entry(int u, int v) { return (u & 3) == 0 && (v & 3) == 0; }
+constexpr uint32_t kTieFreeBits = 0xFFFu;   // (M & kTieFreeBits) != 0  <=>  k <= 11
+
+// Clamp to 0..255 in one instruction: max(min(v, 255), 0).
+__device__ __forceinline__ int clamp_u8(int v) { return __vimin_s32_relu(v, 255); }
+
 // statistics word layout (per plane)
 enum : int {
     kStBand = 0,         // 64 words: sum over blocks of (|Y_uv| >> kBandShift)^2
@@ -356,18 +372,22 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             }
         }
 
-        // Quantiser q = sgn(Y) ((|Y| M + 2^31) >> 32).  The fused kernels use
-        // the high word of the signed Y * M + 2^31 - [Y < 0] (for Y < 0,
-        // floor((Y M + 2^31 - 1) / 2^32) = -floor((|Y| M + 2^31) / 2^32), so
-        // both signs round half away from zero exactly as the definition);
-        // the forward-only kernels are faster with |Y|, an unsigned multiply
-        // and the sign (both forms measured on this GPU).
+        // Quantiser q = sgn(Y) ((|Y| M + 2^31) >> 32).  Away from the four
+        // tie entries the high word of Y M + 2^31 is exact (tie_entry).  At
+        // the tie entries the fused kernels use the high word of the signed
+        // Y * M + 2^31 - [Y < 0] (for Y < 0, floor((Y M + 2^31 - 1) / 2^32) =
+        // -floor((|Y| M + 2^31) / 2^32), so both signs round half away from
+        // zero exactly as the definition); the forward-only kernels use |Y|,
+        // an unsigned multiply and the sign.
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const int y = x[u][v];
-                if (MODE & kInverse) {
+                if (!tie_entry(u, v)) {
+                    const long long p = (long long)y * (long long)(int)T.M[u * 8 + v] + 0x80000000ll;
+                    x[u][v] = (int)(p >> 32);
+                } else if (MODE & kInverse) {
                     const unsigned c = 0x80000000u ^ (unsigned)(y >> 31);
                     const long long p = (long long)y * (long long)(int)T.M[u * 8 + v] + (long long)c;
                     x[u][v] = (int)(p >> 32);
@@ -461,7 +481,7 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
                 uint32_t wd = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int v = max(0, min(255, x[r][4 * h + k] >> (kR + 3)));
+                    const int v = clamp_u8(x[r][4 * h + k] >> (kR + 3));
                     wd |= (uint32_t)v << (8 * k);
                 }
                 out[r][h] = wd;

@@ -1,0 +1,278 @@
+// Fused codec tile with two lanes per 8x8 block.
+//
+// The one-lane-per-block tile (kernels.cuh) keeps all 64 samples of a block
+// in one thread, which makes the row/column transpose free but needs about
+// 128 registers, so only 16 warps fit on an SM; the path is bound by integer
+// issue, and 16 warps leave about a quarter of the issue slots idle on
+// dependency and pipe-throttle stalls.  Here lanes 2k and 2k+1 share block k
+// of a 16-block half tile: lane h owns rows 4h..4h+3 for the row passes and
+// columns 4h..4h+3 for the column passes, 32 values in registers, and the two
+// transposes go through a padded per-warp shared-memory slot (8 stores and 8
+// loads of 16 bytes per lane each, no bank conflicts).  The arithmetic is the
+// same integer graph in the same order as the one-lane tile, so every output
+// is bit-identical to it.
+//
+// Transpose slot of block k (kXSlot bytes): row r, column quad q (columns
+// 4q..4q+3, four int32) at k*kXSlot + (r>>2)*kXRowHalf + (r&3)*32 + q*16.
+// With kXSlot/16 = 2 and kXRowHalf/16 = 1 (mod 8), the 16-byte bank group of
+// an access is (lane + const) mod 8 both when lane h writes its rows and when
+// it reads its column quad, so each quarter-warp phase hits 8 distinct
+// groups.
+#pragma once
+#include "kernels.cuh"
+
+#ifndef DCTGB_PAIR_MINB
+#define DCTGB_PAIR_MINB 4   // resident CTAs of 256 threads per SM (launch bounds: <= 64 registers)
+#endif
+
+namespace dctgb {
+
+constexpr int kPairBlocks = kTileBlocks / 2;      // blocks per half tile
+constexpr int kXSlot = 288;                       // transpose bytes per block
+constexpr int kXRowHalf = 144;                    // offset of rows 4..7 in a slot
+constexpr int kXBytes = kPairBlocks * kXSlot;     // per warp
+static_assert(kPairBlocks * 128 <= kXBytes, "coefficient stage must fit the transpose buffer");
+
+// Shared memory per warp of the two-lane batched kernel: tables, descriptor,
+// transpose buffer (also the coefficient stage).
+__host__ __device__ constexpr int pair_warp_smem_bytes() {
+    return (int)sizeof(QuantSet) + kDescBytes + kXBytes;
+}
+
+// The two-lane tile implements the fused modes (samples in, inverse out).
+__host__ __device__ constexpr bool pair_mode_supported(unsigned mode) {
+    return (mode & kLoadPix) && (mode & kInverse) && !(mode & (kLoadCoef | kStats | kStatsPrivate));
+}
+
+// Loads rows 4h..4h+3 of block (by, bx) as two little-endian words each,
+// with edge replication outside the plane.
+__device__ __forceinline__ void load_rows4(const uint8_t* __restrict__ src, int pitch, int w, int hgt,
+                                           int by, int bx, int h, bool vec, uint32_t (&pix)[4][2]) {
+    const int x0 = bx * 8, y0 = by * 8 + 4 * h;
+    if (vec && x0 + 8 <= w && by * 8 + 8 <= hgt) {
+        const uint8_t* p = src + (size_t)y0 * pitch + x0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(p + (size_t)j * pitch));
+            pix[j][0] = v.x;
+            pix[j][1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int yy = min(y0 + j, hgt - 1);
+            const uint8_t* row = src + (size_t)yy * pitch;
+            uint32_t wd[2] = {0u, 0u};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int xx = min(x0 + c, w - 1);
+                wd[c >> 2] |= (uint32_t)__ldg(row + xx) << (8 * (c & 3));
+            }
+            pix[j][0] = wd[0];
+            pix[j][1] = wd[1];
+        }
+    }
+}
+
+// Stores the in-plane part of rows 4h..4h+3 of block (by, bx).
+__device__ __forceinline__ void store_rows4(uint8_t* __restrict__ dst, int pitch, int w, int hgt,
+                                            int by, int bx, int h, bool vec, const uint32_t (&pix)[4][2]) {
+    const int x0 = bx * 8, y0 = by * 8 + 4 * h;
+    if (vec && x0 + 8 <= w && by * 8 + 8 <= hgt) {
+        uint8_t* p = dst + (size_t)y0 * pitch + x0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<uint2*>(p + (size_t)j * pitch) = make_uint2(pix[j][0], pix[j][1]);
+    } else {
+        const int nr = min(4, hgt - y0), nc = min(8, w - x0);
+        for (int j = 0; j < nr; ++j) {
+            uint8_t* row = dst + (size_t)(y0 + j) * pitch + x0;
+            for (int c = 0; c < nc; ++c) row[c] = (uint8_t)(pix[j][c >> 2] >> (8 * (c & 3)));
+        }
+    }
+}
+
+__device__ __forceinline__ int sample4(const uint32_t (&pix)[4][2], int j, int c) {
+    return (int)((pix[j][c >> 2] >> (8 * (c & 3))) & 0xFFu);
+}
+
+__device__ __forceinline__ void sts128(uint8_t* p, int a, int b, int c, int d) {
+    *reinterpret_cast<int4*>(p) = make_int4(a, b, c, d);
+}
+__device__ __forceinline__ int4 lds128(const uint8_t* p) { return *reinterpret_cast<const int4*>(p); }
+
+// Processes warp tile `tile_in_plane` of plane P (two half tiles of 16
+// blocks).  xb is this warp's kXBytes transpose buffer.  Returns the tile's
+// SSE (the same in every lane; 0 without kSse).
+template <unsigned MODE>
+__device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const QuantSet& T, int tile_in_plane,
+                                                      int lane, uint8_t* xb) {
+    static_assert(pair_mode_supported(MODE), "two-lane tile implements the fused modes only");
+    const int k = lane >> 1, h = lane & 1;
+    uint8_t* const xw = xb + k * kXSlot + h * kXRowHalf;   // rows 4h..4h+3, both quads
+    uint8_t* const xr = xb + k * kXSlot + h * 16;           // rows 0..7, quad h
+    // descale rounding term and +128 level, added once to the DC input
+    // (column 0 belongs to lane h = 0)
+    const int dc_bias = h ? 0 : (1 << (kR + 2)) + (128 << (kR + 3));
+    const int32_t* Mh = reinterpret_cast<const int32_t*>(T.M) + 4 * h;
+    const int32_t* QWh = T.QW + 4 * h;
+    unsigned e = 0;
+
+#pragma unroll 1
+    for (int hf = 0; hf < 2; ++hf) {
+        const int b0 = tile_in_plane * kTileBlocks + hf * kPairBlocks;
+        const int nvalid = min(kPairBlocks, P.nblk - b0);
+        if (nvalid <= 0) break;                      // warp-uniform
+        const bool active = k < nvalid;
+        int by = 0, bx = 0;
+        if (active) {
+            by = (b0 + k) / P.nbx;
+            bx = b0 + k - by * P.nbx;
+        }
+
+        // level shift and row pass on rows 4h..4h+3
+        int v[4][8];
+        uint32_t pix[4][2];
+        {
+            if (active) {
+                load_rows4(P.src, P.src_pitch, P.width, P.height, by, bx, h, (P.flags & kVecSrc) != 0, pix);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) pix[j][0] = pix[j][1] = 0x80808080u;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[j][c] = (sample4(pix, j, c) - 128) * (1 << kP);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) loeffler8_fwd(v[j]);
+
+        // transpose: rows 4h..4h+3 out, columns 4h..4h+3 in
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            sts128(xw + j * 32, v[j][0], v[j][1], v[j][2], v[j][3]);
+            sts128(xw + j * 32 + 16, v[j][4], v[j][5], v[j][6], v[j][7]);
+        }
+        __syncwarp();
+        int c[4][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int4 t = lds128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32);
+            c[0][r] = t.x;
+            c[1][r] = t.y;
+            c[2][r] = t.z;
+            c[3][r] = t.w;
+        }
+
+        // column pass: c[i][u] = Y[u][4h + i]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) loeffler8_fwd(c[i]);
+
+        // quantiser: high word of Y M + 2^31, with - [Y < 0] at the tie
+        // entries (u, v in {0, 4}: i = 0 and u = 0 or 4 in both lanes)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int4 m = *reinterpret_cast<const int4*>(Mh + u * 8);
+            const int mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int y = c[i][u];
+                long long p = (long long)y * (long long)mv[i] + 0x80000000ll;
+                if (tie_entry(u, i)) p += (long long)(y >> 31);
+                c[i][u] = (int)(p >> 32);
+            }
+        }
+
+        if (MODE & kStoreCoef) {
+            __syncwarp();                            // transpose reads done
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint2 w = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
+                                           ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
+                *reinterpret_cast<uint2*>(xb + stage_off(k, u) + 8 * h) = w;
+            }
+            __syncwarp();
+            uint4* g = reinterpret_cast<uint4*>(P.coef + (size_t)b0 * 64);
+#pragma unroll
+            for (int it = 0; it < kPairBlocks * 8 / 32; ++it) {
+                const int cc = it * 32 + lane;
+                const int blk = cc >> 3;
+                if (blk < nvalid) g[cc] = *reinterpret_cast<const uint4*>(xb + stage_off(blk, cc & 7));
+            }
+        }
+
+        // dequantiser G = q (Q W): the clamp of the definition never acts on
+        // this kernel's own codes (|q Q| < 1200)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
+            c[0][u] *= qw.x;
+            c[1][u] *= qw.y;
+            c[2][u] *= qw.z;
+            c[3][u] *= qw.w;
+        }
+        c[0][0] += dc_bias;
+
+        // inverse column pass, transpose back, inverse row pass
+#pragma unroll
+        for (int i = 0; i < 4; ++i) loeffler8_inv(c[i]);
+        __syncwarp();                                // stage / transpose reads done
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sts128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32, c[0][r], c[1][r], c[2][r], c[3][r]);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int4 a = lds128(xw + j * 32);
+            const int4 b = lds128(xw + j * 32 + 16);
+            v[j][0] = a.x; v[j][1] = a.y; v[j][2] = a.z; v[j][3] = a.w;
+            v[j][4] = b.x; v[j][5] = b.y; v[j][6] = b.z; v[j][7] = b.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) loeffler8_inv(v[j]);
+
+        // descale, clamp, pack
+        uint32_t out[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t wd = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int s = clamp_u8(v[j][4 * q + t] >> (kR + 3));
+                    wd |= (uint32_t)s << (8 * t);
+                }
+                out[j][q] = wd;
+            }
+        }
+        if ((MODE & kStoreRecon) && active)
+            store_rows4(P.dst, P.dst_pitch, P.width, P.height, by, bx, h, (P.flags & kVecDst) != 0, out);
+
+        if ((MODE & kSse) && active) {
+            const int nr = min(4, P.height - (by * 8 + 4 * h)), nc = min(8, P.width - bx * 8);
+            if (nr == 4 && nc == 8) {
+                unsigned rr = 0, pp = 0, rp = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        rr = __dp4a(out[j][q], out[j][q], rr);
+                        pp = __dp4a(pix[j][q], pix[j][q], pp);
+                        rp = __dp4a(out[j][q], pix[j][q], rp);
+                    }
+                e += rr + pp - 2u * rp;
+            } else {
+                for (int j = 0; j < nr; ++j)
+                    for (int cc = 0; cc < nc; ++cc) {
+                        const int d = sample4(out, j, cc) - sample4(pix, j, cc);
+                        e += d * d;
+                    }
+            }
+        }
+    }
+    return (MODE & kSse) ? warp_sum(e) : 0u;
+}
+
+}  // namespace dctgb

@@ -60,7 +60,7 @@ class dct_batch_item(ctypes.Structure):
 
 class dct_launch_shape(ctypes.Structure):
     _fields_ = [("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("tile_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_blocks", ctypes.c_int32), ("lanes_per_block", ctypes.c_int32)]
 
 
 DCT_MLP_INPUTS = 80
@@ -433,11 +433,11 @@ def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
 
 def dct_autotune(plan, stream=None):
     """Times candidate launch shapes for the prepared batch; returns
-    ((threads, ctas_per_sm, tile_blocks, 0), best ms)."""
+    ((threads, ctas_per_sm, tile_blocks, lanes_per_block), best ms)."""
     sh = dct_launch_shape()
     ms = ctypes.c_float()
     _check(load().dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)))
-    return (sh.threads_per_cta, sh.ctas_per_sm, sh.tile_blocks, sh.reserved), ms.value
+    return (sh.threads_per_cta, sh.ctas_per_sm, sh.tile_blocks, sh.lanes_per_block), ms.value
 
 
 def autotune_cached(plan, items, ops, sse=None, cache_path=None, key=None, stream=None):

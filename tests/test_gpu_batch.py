@@ -57,7 +57,8 @@ def run_batch(D, plan, items, ops, shape=None, launches=1):
     return coefs, recs, sse, srcs, arr
 
 
-@pytest.mark.parametrize("shape", [None, (64, 1, 32, 0), (256, 2, 32, 0), (128, 16, 32, 0)])
+@pytest.mark.parametrize("shape", [None, (64, 1, 32, 0), (256, 2, 32, 0), (128, 16, 32, 0),
+                                   (64, 1, 32, 2), (256, 4, 32, 2), (128, 16, 32, 2)])
 def test_batch_fused_matches_oracle(D, shape):
     items = make_items(24, seed=1)
     with D.Plan(512, 512, max_batch=64) as plan:
@@ -70,14 +71,16 @@ def test_batch_fused_matches_oracle(D, shape):
             assert int(sse[i]) == s_or, i
 
 
-@pytest.mark.parametrize("mode", ["compress", "sse_only", "compress_sse", "recon_sse", "twopass", "twopass_nosse"])
-def test_batch_op_combinations(D, mode):
+@pytest.mark.parametrize("lanes", [1, 2])
+@pytest.mark.parametrize("mode", ["compress", "sse_only", "compress_sse", "recon_sse", "recon_only", "twopass",
+                                  "twopass_nosse"])
+def test_batch_op_combinations(D, mode, lanes):
     items = make_items(12, seed=2)
     C, R, S, T = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE, D.DCT_OP_TWO_PASS
-    ops = {"compress": C, "sse_only": S, "compress_sse": C | S, "recon_sse": C | R | S,
+    ops = {"compress": C, "sse_only": S, "compress_sse": C | S, "recon_sse": C | R | S, "recon_only": C | R,
            "twopass": C | R | S | T, "twopass_nosse": C | R | T}[mode]
     with D.Plan(512, 512, max_batch=16) as plan:
-        coefs, recs, sse, _, _ = run_batch(D, plan, items, ops)
+        coefs, recs, sse, _, _ = run_batch(D, plan, items, ops, shape=(128, 2, 32, lanes))
         for i, it in enumerate(items):
             c_or, r_or, s_or = oracle(it)
             if ops & C:
@@ -211,10 +214,11 @@ def test_batch_invalid_arguments(D):
             D.dct_batch_prepare(plan, D.make_batch_items([t], [50], coeffs=[c]), D.DCT_OP_COMPRESS)
 
 
-def test_batch_maximum_plane_sampled(D):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_batch_maximum_plane_sampled(D, lanes):
     """The largest plane a plan accepts below 2^31 samples, 32767 x 65535
     (ragged in both directions), through the fused batch in the benchmark's
-    launch shape: the last block row and column and 1024 random interior
+    launch shapes (one and two lanes per block): the last block row and column and 1024 random interior
     blocks against the oracle, the SSE against the reconstruction."""
     h, w = 32767, 65535
     quality = 50
@@ -228,7 +232,7 @@ def test_batch_maximum_plane_sampled(D):
         sse = torch.zeros(1, dtype=torch.int64, device="cuda")
         arr = D.make_batch_items([src], [quality], coeffs=[coef], recons=[rec])
         D.dct_batch_prepare(plan, arr, D.DCT_OP_COMPRESS | D.DCT_OP_RECONSTRUCT | D.DCT_OP_SSE, sse=sse,
-                            shape=(256, 16, 32, 0))
+                            shape=(256, 16, 32, lanes))
         D.dct_batch_launch(plan)
         torch.cuda.synchronize()
     Q = ijg.luma_table(quality)
