@@ -46,6 +46,8 @@ def parse():
                     help="threads,ctas_per_sm[,lanes_per_block]: fixed launch shape, no autotuning")
     ap.add_argument("--no-ratecontrol", action="store_true", help="skip the learned-rate-control workloads")
     ap.add_argument("--rc-epochs", type=int, default=300)
+    ap.add_argument("--no-context", action="store_true",
+                    help="skip the untimed context fields (Tables 3-4 PSNR, rate, paper sizes, 512-image batch)")
     return ap.parse_args()
 
 
@@ -115,7 +117,7 @@ def algorithmic_ops_per_sample():
     return 2 + 2 * per_pass + 5 + 4 + 2 * per_pass + 5 + 3
 
 
-KERNEL_SOURCES = ("batch.cu", "kernels.cuh", "cordic_loeffler.cuh", "dctgb_spec.h")
+KERNEL_SOURCES = ("batch.cu", "kernels.cuh", "kernels_pair.cuh", "cordic_loeffler.cuh", "dctgb_spec.h")
 
 
 def kernel_sources_sha():
@@ -715,7 +717,8 @@ def main():
     ops = algorithmic_ops_per_sample()
     bytes_per_sample = 4 if args.path == "fused" else 7
     if args.path == "fused":
-        kernel = "k_batch<fused: load, fwd, quant, store coef, dequant, inv, store recon, SSE>"
+        kernel = "%s<fused: load, fwd, quant, store coef, dequant, inv, store recon, SSE>" % (
+            "k_batch_pair" if shape[3] == 2 else "k_batch")
         note = "event interval per step covers the SSE-clear kernel (about 1%) and the fused kernel"
     else:
         kernel = "k_batch<two-pass: forward + inverse>"
@@ -752,12 +755,14 @@ def main():
         line["cpu_baseline"] = cpu_baseline_parallel(host_grey, args.cpu_seconds)
         line["cpu_baseline"]["single_thread"] = single
     plan.close()
-    line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
-    line["rate"] = rate_of_coefficients(D, coefs, shapes)
-    line["paper_sizes"] = paper_size_sweep(D, dev)
+    if not args.no_context:
+        line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
+        line["rate"] = rate_of_coefficients(D, coefs, shapes)
+        line["paper_sizes"] = paper_size_sweep(D, dev)
     del planes, coefs, recons, flush
     torch.cuda.empty_cache()
-    line["batch512"] = batch512(D, dev, roof["ops_per_sample"], roof["peak"], roof["hbm"]["peak"])
+    if not args.no_context:
+        line["batch512"] = batch512(D, dev, roof["ops_per_sample"], roof["peak"], roof["hbm"]["peak"])
     if not args.no_ratecontrol:
         line["ratecontrol"] = {"grey": rc_grey(dev, args.rc_epochs), "stream420": rc_stream(dev, args.rc_epochs)}
     if rank == 0:

@@ -234,10 +234,13 @@ typedef struct {
     const uint16_t* qtab_host; /* 64 entries when quality == 0, else NULL */
 } dct_batch_item;
 
-/* Launch shape of the persistent kernel, chosen by dct_autotune. */
+/* Launch shape of the persistent kernel, chosen by dct_autotune.  A new
+ * plan starts with {256, 8, 32, 2}. */
 typedef struct {
     int32_t threads_per_cta;   /* 64..256, multiple of 32 */
-    int32_t ctas_per_sm;       /* >= 1 */
+    int32_t ctas_per_sm;       /* 1..32 CTAs per SM in the grid (more than fit
+                                * at once: shorter tile ranges); 0: as many
+                                * as fit at once */
     int32_t tile_blocks;       /* 8x8 blocks per warp tile: 32 */
     int32_t lanes_per_block;   /* 0 or 1: one lane per 8x8 block; 2: two lanes
                                 * per block (fused COMPRESS/RECONSTRUCT/SSE
@@ -268,7 +271,13 @@ dct_status dct_batch_launch(dct_plan_t plan, dct_stream_t stream);
 /* Times candidate launch shapes for the prepared batch (CUDA events on
  * `stream`, which is synchronised), keeps the fastest as the plan's shape,
  * re-captures the graph with it and writes it to *best (may be NULL).
- * ms_host (may be NULL) receives the best time in milliseconds. */
+ * ms_host (may be NULL) receives the best time in milliseconds.  The
+ * candidates are 64/128/256 threads per CTA x 1..16 CTAs per SM, with one
+ * and (fused operations) two lanes per block.  Every timed replay follows a
+ * write over twice the L2 size into a temporary device buffer, so the
+ * choice holds for inputs that are not already cached; if that buffer
+ * cannot be allocated the replays run warm.  Replays the batch's kernels,
+ * so its outputs are overwritten. */
 dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host, dct_stream_t stream);
 
 /* ---------------------------------------------------------------------

@@ -194,10 +194,7 @@ dct_status dct_plan_create(dct_plan_t* out, const dct_plan_desc* desc, dct_strea
     p->desc = *desc;
     p->device = dev;
     p->num_sms = sms;
-    p->shape.threads_per_cta = 256;
-    p->shape.ctas_per_sm = 0;     // 0: use the occupancy-derived default
-    p->shape.tile_blocks = kTileBlocks;
-    p->shape.lanes_per_block = 0;
+    p->shape = default_shape();
     p->batch = nullptr;
     p->rc = nullptr;
     *out = p;

@@ -39,6 +39,11 @@ struct dct_plan_s {
 
 namespace dctgb {
 
+// Launch shape of the batched kernels until dct_autotune picks one: 256
+// threads, 8 CTAs per SM (oversubscribed: shorter contiguous tile ranges),
+// two lanes per block for the fused operations.
+inline dct_launch_shape default_shape() { return dct_launch_shape{256, 8, kTileBlocks, 2}; }
+
 // Checks one plane against the plan limits; `what` names it in errors.
 dct_status check_plane(const dct_plan_s* plan, const dct_plane& p, const char* what);
 

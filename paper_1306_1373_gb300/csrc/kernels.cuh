@@ -496,17 +496,15 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
             if (active) {
                 const int nr = min(8, P.height - by * 8), nc = min(8, P.width - bx * 8);
                 if (nr == 8 && nc == 8) {
-                    // sum (r - p)^2 = sum r^2 + sum p^2 - 2 sum r p, four bytes per dp4a
-                    unsigned rr = 0, pp = 0, rp = 0;
+                    // |r - p| per byte (vabsdiffu4), then the four squares and their
+                    // sum in one dp4a
 #pragma unroll
                     for (int r = 0; r < 8; ++r)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            rr = __dp4a(out[r][h], out[r][h], rr);
-                            pp = __dp4a(pix[r][h], pix[r][h], pp);
-                            rp = __dp4a(out[r][h], pix[r][h], rp);
+                            const unsigned ad = __vabsdiffu4(out[r][h], pix[r][h]);
+                            e = __dp4a(ad, ad, e);
                         }
-                    e = rr + pp - 2u * rp;
                 } else {
                     for (int r = 0; r < nr; ++r)
                         for (int c = 0; c < nc; ++c) {

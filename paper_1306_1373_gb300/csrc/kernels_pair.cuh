@@ -8,9 +8,12 @@
 // of a 16-block half tile: lane h owns rows 4h..4h+3 for the row passes and
 // columns 4h..4h+3 for the column passes, 32 values in registers, and the two
 // transposes go through a padded per-warp shared-memory slot (8 stores and 8
-// loads of 16 bytes per lane each, no bank conflicts).  The arithmetic is the
-// same integer graph in the same order as the one-lane tile, so every output
-// is bit-identical to it.
+// loads of 16 bytes per lane each, no bank conflicts).  To stay within 64
+// registers with few spills, the samples wait for the SSE in a per-lane
+// shared-memory slot, and the coefficients go straight from registers to
+// global memory (8 bytes per lane and row: the lane pair fills the row's 16
+// bytes).  The arithmetic is the same integer graph in the same order as the
+// one-lane tile, so every output is bit-identical to it.
 //
 // Transpose slot of block k (kXSlot bytes): row r, column quad q (columns
 // 4q..4q+3, four int32) at k*kXSlot + (r>>2)*kXRowHalf + (r&3)*32 + q*16.
@@ -31,12 +34,12 @@ constexpr int kPairBlocks = kTileBlocks / 2;      // blocks per half tile
 constexpr int kXSlot = 288;                       // transpose bytes per block
 constexpr int kXRowHalf = 144;                    // offset of rows 4..7 in a slot
 constexpr int kXBytes = kPairBlocks * kXSlot;     // per warp
-static_assert(kPairBlocks * 128 <= kXBytes, "coefficient stage must fit the transpose buffer");
+constexpr int kParkBytes = 32 * 32;               // each lane's 32 samples, kept for the SSE
 
 // Shared memory per warp of the two-lane batched kernel: tables, descriptor,
-// transpose buffer (also the coefficient stage).
+// transpose buffer, sample slots.
 __host__ __device__ constexpr int pair_warp_smem_bytes() {
-    return (int)sizeof(QuantSet) + kDescBytes + kXBytes;
+    return (int)sizeof(QuantSet) + kDescBytes + kXBytes + kParkBytes;
 }
 
 // The two-lane tile implements the fused modes (samples in, inverse out).
@@ -102,8 +105,9 @@ __device__ __forceinline__ void sts128(uint8_t* p, int a, int b, int c, int d) {
 __device__ __forceinline__ int4 lds128(const uint8_t* p) { return *reinterpret_cast<const int4*>(p); }
 
 // Processes warp tile `tile_in_plane` of plane P (two half tiles of 16
-// blocks).  xb is this warp's kXBytes transpose buffer.  Returns the tile's
-// SSE (the same in every lane; 0 without kSse).
+// blocks).  xb is this warp's kXBytes transpose buffer followed by its
+// kParkBytes sample slots.  Returns the tile's SSE (the same in every lane;
+// 0 without kSse).
 template <unsigned MODE>
 __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const QuantSet& T, int tile_in_plane,
                                                       int lane, uint8_t* xb) {
@@ -116,38 +120,52 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
     const int dc_bias = h ? 0 : (1 << (kR + 2)) + (128 << (kR + 3));
     const int32_t* Mh = reinterpret_cast<const int32_t*>(T.M) + 4 * h;
     const int32_t* QWh = T.QW + 4 * h;
+    uint8_t* const park = xb + kXBytes + lane * 32;
+    const int psw = (lane >> 2) & 1;
     unsigned e = 0;
+    // block coordinates: one division per tile, then steps of 16 blocks
+    const int bt = tile_in_plane * kTileBlocks;
+    const int by_t = bt / P.nbx;
+    const int bx_t = bt - by_t * P.nbx;
 
 #pragma unroll 1
     for (int hf = 0; hf < 2; ++hf) {
-        const int b0 = tile_in_plane * kTileBlocks + hf * kPairBlocks;
+        const int b0 = bt + hf * kPairBlocks;
         const int nvalid = min(kPairBlocks, P.nblk - b0);
         if (nvalid <= 0) break;                      // warp-uniform
         const bool active = k < nvalid;
-        int by = 0, bx = 0;
-        if (active) {
-            by = (b0 + k) / P.nbx;
-            bx = b0 + k - by * P.nbx;
+        int by = by_t, bx = bx_t + hf * kPairBlocks + k;
+        if (bx >= P.nbx) {
+            bx -= P.nbx;
+            ++by;
+            if (bx >= P.nbx) {                       // planes narrower than 32 blocks
+                by += bx / P.nbx;
+                bx -= (bx / P.nbx) * P.nbx;
+            }
         }
 
         // level shift and row pass on rows 4h..4h+3
         int v[4][8];
         uint32_t pix[4][2];
-        {
-            if (active) {
-                load_rows4(P.src, P.src_pitch, P.width, P.height, by, bx, h, (P.flags & kVecSrc) != 0, pix);
-            } else {
+        if (active) {
+            load_rows4(P.src, P.src_pitch, P.width, P.height, by, bx, h, (P.flags & kVecSrc) != 0, pix);
+        } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) pix[j][0] = pix[j][1] = 0x80808080u;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[j][c] = (sample4(pix, j, c) - 128) * (1 << kP);
+            for (int j = 0; j < 4; ++j) pix[j][0] = pix[j][1] = 0x80808080u;
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[j][c] = (sample4(pix, j, c) - 128) * (1 << kP);
 #pragma unroll
         for (int j = 0; j < 4; ++j) loeffler8_fwd(v[j]);
 
+        // the samples wait for the SSE in this lane's slot (the two 16-byte
+        // halves swap on every fourth lane: no bank conflicts)
+        if (MODE & kSse) {
+            *reinterpret_cast<uint4*>(park + 16 * psw) = make_uint4(pix[0][0], pix[0][1], pix[1][0], pix[1][1]);
+            *reinterpret_cast<uint4*>(park + 16 * (psw ^ 1)) = make_uint4(pix[2][0], pix[2][1], pix[3][0], pix[3][1]);
+        }
         // transpose: rows 4h..4h+3 out, columns 4h..4h+3 in
         __syncwarp();
 #pragma unroll
@@ -185,22 +203,13 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
             }
         }
 
-        if (MODE & kStoreCoef) {
-            __syncwarp();                            // transpose reads done
+        // coefficients: row u of the block is 16 bytes, lane h writes its half
+        if ((MODE & kStoreCoef) && active) {
+            uint2* g = reinterpret_cast<uint2*>(P.coef + (size_t)(b0 + k) * 64 + 4 * h);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint2 w = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
-                                           ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
-                *reinterpret_cast<uint2*>(xb + stage_off(k, u) + 8 * h) = w;
-            }
-            __syncwarp();
-            uint4* g = reinterpret_cast<uint4*>(P.coef + (size_t)b0 * 64);
-#pragma unroll
-            for (int it = 0; it < kPairBlocks * 8 / 32; ++it) {
-                const int cc = it * 32 + lane;
-                const int blk = cc >> 3;
-                if (blk < nvalid) g[cc] = *reinterpret_cast<const uint4*>(xb + stage_off(blk, cc & 7));
-            }
+            for (int u = 0; u < 8; ++u)
+                g[2 * u] = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
+                                      ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
         }
 
         // dequantiser G = q (Q W): the clamp of the definition never acts on
@@ -218,7 +227,7 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
         // inverse column pass, transpose back, inverse row pass
 #pragma unroll
         for (int i = 0; i < 4; ++i) loeffler8_inv(c[i]);
-        __syncwarp();                                // stage / transpose reads done
+        __syncwarp();                                // transpose reads done
 #pragma unroll
         for (int r = 0; r < 8; ++r) sts128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32, c[0][r], c[1][r], c[2][r], c[3][r]);
         __syncwarp();
@@ -251,18 +260,21 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
             store_rows4(P.dst, P.dst_pitch, P.width, P.height, by, bx, h, (P.flags & kVecDst) != 0, out);
 
         if ((MODE & kSse) && active) {
+            {
+                const uint4 a = *reinterpret_cast<const uint4*>(park + 16 * psw);
+                const uint4 b = *reinterpret_cast<const uint4*>(park + 16 * (psw ^ 1));
+                pix[0][0] = a.x; pix[0][1] = a.y; pix[1][0] = a.z; pix[1][1] = a.w;
+                pix[2][0] = b.x; pix[2][1] = b.y; pix[3][0] = b.z; pix[3][1] = b.w;
+            }
             const int nr = min(4, P.height - (by * 8 + 4 * h)), nc = min(8, P.width - bx * 8);
             if (nr == 4 && nc == 8) {
-                unsigned rr = 0, pp = 0, rp = 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        rr = __dp4a(out[j][q], out[j][q], rr);
-                        pp = __dp4a(pix[j][q], pix[j][q], pp);
-                        rp = __dp4a(out[j][q], pix[j][q], rp);
+                        const unsigned ad = __vabsdiffu4(out[j][q], pix[j][q]);
+                        e = __dp4a(ad, ad, e);
                     }
-                e += rr + pp - 2u * rp;
             } else {
                 for (int j = 0; j < nr; ++j)
                     for (int cc = 0; cc < nc; ++cc) {
