@@ -413,6 +413,49 @@ def paper_size_sweep(D, dev, reps=50):
     return out
 
 
+def direct_api(D, dev, planes, flush, sse_ref, reps=30):
+    """The plane calls of the boundary on the benchmark planes, one call for
+    the grey plane and one for the 4:2:0 frame per step, L2 flushed between
+    steps: dct_codec_fused (coefficients, reconstruction and SSE in one
+    pass) and dct_compress + dct_reconstruct (with SSE)."""
+    import torch
+    grey, frame = planes[:1], planes[1:]
+    samples = sum(int(p.numel()) for p in planes)
+    out = {"unit": "MPix/s", "steps": reps}
+    with D.Plan(8192, 8192) as pg, D.Plan(3840, 2160, layout=D.DCT_LAYOUT_YUV420) as pf:
+        sets = []
+        for plan, ps in ((pg, grey), (pf, frame)):
+            coef = torch.empty(D.coeff_count([tuple(p.shape) for p in ps]), dtype=torch.int16, device=dev)
+            rec = D.PlaneArray([torch.empty_like(p) for p in ps])
+            sets.append((plan, D.PlaneArray(ps), coef, rec, torch.zeros(len(ps), dtype=torch.int64, device=dev)))
+
+        def fused():
+            for plan, src, coef, rec, sse in sets:
+                D.dct_codec_fused(plan, src, QUALITY, coeffs=coef, recon_planes=rec, sse=sse)
+
+        def two_calls():
+            for plan, src, coef, rec, sse in sets:
+                D.dct_compress(plan, src, QUALITY, coeffs=coef)
+                D.dct_reconstruct(plan, coef, rec, QUALITY, ref_planes=src, sse=sse)
+
+        stream = torch.cuda.current_stream()
+        for name, fn in (("codec_fused", fused), ("compress_reconstruct", two_calls)):
+            for _ in range(3):
+                flush.zero_()
+                fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for k in range(reps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+            sse_now = [int(v) for st in sets for v in st[4].tolist()]
+            out[name] = {"ms": ms, "mpix_s": samples / (ms * 1e-3) / 1e6, "sse_matches_batched_run": sse_now == sse_ref}
+    return out
+
+
 def batch512(D, dev, ops_per_sample, alu_peak_tops, hbm_gbs, reps=20):
     """The batched workload of uneven images: 512 grey planes, W and H
     multiples of 8 in [64, 2048], quality 10..95, 1/f^beta content with beta
@@ -759,6 +802,7 @@ def main():
         line["tables34_psnr"] = exact_vs_cordic(D, planes, chroma)
         line["rate"] = rate_of_coefficients(D, coefs, shapes)
         line["paper_sizes"] = paper_size_sweep(D, dev)
+        line["direct_api"] = direct_api(D, dev, planes, flush, [int(v) for v in sse_h])
     del planes, coefs, recons, flush
     torch.cuda.empty_cache()
     if not args.no_context:

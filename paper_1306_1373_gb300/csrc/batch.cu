@@ -226,6 +226,9 @@ using KernelPtr = void (*)(BatchArgs);
 
 static KernelPtr pair_kernel(unsigned mode) {
     switch (mode) {
+        case kLoadPix | kStoreCoef: return k_batch_pair<kLoadPix | kStoreCoef>;
+        case kLoadCoef | kInverse | kStoreRecon: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon>;
+        case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kSse>;
         case kLoadPix | kInverse | kSse: return k_batch_pair<kLoadPix | kInverse | kSse>;
         case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef>;
         case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreRecon>;

@@ -42,9 +42,14 @@ __host__ __device__ constexpr int pair_warp_smem_bytes() {
     return (int)sizeof(QuantSet) + kDescBytes + kXBytes + kParkBytes;
 }
 
-// The two-lane tile implements the fused modes (samples in, inverse out).
+// The two-lane tile implements the fused modes (samples in, inverse out),
+// the forward pass alone (samples in, coefficients out) and the inverse pass
+// alone (coefficients in, reconstruction and/or SSE out); the statistics
+// modes keep the one-lane tile.
 __host__ __device__ constexpr bool pair_mode_supported(unsigned mode) {
-    return (mode & kLoadPix) && (mode & kInverse) && !(mode & (kLoadCoef | kStats | kStatsPrivate));
+    return !(mode & (kStats | kStatsPrivate)) &&
+           (((mode & kLoadPix) && !(mode & kLoadCoef) && ((mode & kInverse) || mode == (kLoadPix | kStoreCoef))) ||
+            ((mode & kLoadCoef) && (mode & kInverse) && !(mode & (kLoadPix | kStoreCoef))));
 }
 
 // Loads rows 4h..4h+3 of block (by, bx) as two little-endian words each,
@@ -104,6 +109,19 @@ __device__ __forceinline__ void sts128(uint8_t* p, int a, int b, int c, int d) {
 }
 __device__ __forceinline__ int4 lds128(const uint8_t* p) { return *reinterpret_cast<const int4*>(p); }
 
+// A lane's four sample rows in its 32-byte slot; the halves swap on every
+// fourth lane so a quarter warp's 16-byte accesses hit distinct bank groups.
+__device__ __forceinline__ void park_rows(uint8_t* slot, int sw, const uint32_t (&pix)[4][2]) {
+    *reinterpret_cast<uint4*>(slot + 16 * sw) = make_uint4(pix[0][0], pix[0][1], pix[1][0], pix[1][1]);
+    *reinterpret_cast<uint4*>(slot + 16 * (sw ^ 1)) = make_uint4(pix[2][0], pix[2][1], pix[3][0], pix[3][1]);
+}
+__device__ __forceinline__ void unpark_rows(const uint8_t* slot, int sw, uint32_t (&pix)[4][2]) {
+    const uint4 a = *reinterpret_cast<const uint4*>(slot + 16 * sw);
+    const uint4 b = *reinterpret_cast<const uint4*>(slot + 16 * (sw ^ 1));
+    pix[0][0] = a.x; pix[0][1] = a.y; pix[1][0] = a.z; pix[1][1] = a.w;
+    pix[2][0] = b.x; pix[2][1] = b.y; pix[3][0] = b.z; pix[3][1] = b.w;
+}
+
 // Processes warp tile `tile_in_plane` of plane P (two half tiles of 16
 // blocks).  xb is this warp's kXBytes transpose buffer followed by its
 // kParkBytes sample slots.  Returns the tile's SSE (the same in every lane;
@@ -111,7 +129,7 @@ __device__ __forceinline__ int4 lds128(const uint8_t* p) { return *reinterpret_c
 template <unsigned MODE>
 __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const QuantSet& T, int tile_in_plane,
                                                       int lane, uint8_t* xb) {
-    static_assert(pair_mode_supported(MODE), "two-lane tile implements the fused modes only");
+    static_assert(pair_mode_supported(MODE), "no two-lane form of this mode");
     const int k = lane >> 1, h = lane & 1;
     uint8_t* const xw = xb + k * kXSlot + h * kXRowHalf;   // rows 4h..4h+3, both quads
     uint8_t* const xr = xb + k * kXSlot + h * 16;           // rows 0..7, quad h
@@ -120,6 +138,8 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
     const int dc_bias = h ? 0 : (1 << (kR + 2)) + (128 << (kR + 3));
     const int32_t* Mh = reinterpret_cast<const int32_t*>(T.M) + 4 * h;
     const int32_t* QWh = T.QW + 4 * h;
+    const int32_t* Qh = T.Q + 4 * h;
+    const int32_t* Wh = T.W + 4 * h;
     uint8_t* const park = xb + kXBytes + lane * 32;
     const int psw = (lane >> 2) & 1;
     unsigned e = 0;
@@ -144,83 +164,115 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
             }
         }
 
-        // level shift and row pass on rows 4h..4h+3
         int v[4][8];
-        uint32_t pix[4][2];
-        if (active) {
-            load_rows4(P.src, P.src_pitch, P.width, P.height, by, bx, h, (P.flags & kVecSrc) != 0, pix);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) pix[j][0] = pix[j][1] = 0x80808080u;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v[j][c] = (sample4(pix, j, c) - 128) * (1 << kP);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) loeffler8_fwd(v[j]);
-
-        // the samples wait for the SSE in this lane's slot (the two 16-byte
-        // halves swap on every fourth lane: no bank conflicts)
-        if (MODE & kSse) {
-            *reinterpret_cast<uint4*>(park + 16 * psw) = make_uint4(pix[0][0], pix[0][1], pix[1][0], pix[1][1]);
-            *reinterpret_cast<uint4*>(park + 16 * (psw ^ 1)) = make_uint4(pix[2][0], pix[2][1], pix[3][0], pix[3][1]);
-        }
-        // transpose: rows 4h..4h+3 out, columns 4h..4h+3 in
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            sts128(xw + j * 32, v[j][0], v[j][1], v[j][2], v[j][3]);
-            sts128(xw + j * 32 + 16, v[j][4], v[j][5], v[j][6], v[j][7]);
-        }
-        __syncwarp();
         int c[4][8];
+        uint32_t pix[4][2];
+        if (MODE & kLoadPix) {
+            // level shift and row pass on rows 4h..4h+3
+            if (active) {
+                load_rows4(P.src, P.src_pitch, P.width, P.height, by, bx, h, (P.flags & kVecSrc) != 0, pix);
+            } else {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int4 t = lds128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32);
-            c[0][r] = t.x;
-            c[1][r] = t.y;
-            c[2][r] = t.z;
-            c[3][r] = t.w;
-        }
-
-        // column pass: c[i][u] = Y[u][4h + i]
-#pragma unroll
-        for (int i = 0; i < 4; ++i) loeffler8_fwd(c[i]);
-
-        // quantiser: high word of Y M + 2^31, with - [Y < 0] at the tie
-        // entries (u, v in {0, 4}: i = 0 and u = 0 or 4 in both lanes)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int4 m = *reinterpret_cast<const int4*>(Mh + u * 8);
-            const int mv[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int y = c[i][u];
-                long long p = (long long)y * (long long)mv[i] + 0x80000000ll;
-                if (tie_entry(u, i)) p += (long long)(y >> 31);
-                c[i][u] = (int)(p >> 32);
+                for (int j = 0; j < 4; ++j) pix[j][0] = pix[j][1] = 0x80808080u;
             }
-        }
-
-        // coefficients: row u of the block is 16 bytes, lane h writes its half
-        if ((MODE & kStoreCoef) && active) {
-            uint2* g = reinterpret_cast<uint2*>(P.coef + (size_t)(b0 + k) * 64 + 4 * h);
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                g[2 * u] = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
-                                      ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
-        }
-
-        // dequantiser G = q (Q W): the clamp of the definition never acts on
-        // this kernel's own codes (|q Q| < 1200)
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
-            c[0][u] *= qw.x;
-            c[1][u] *= qw.y;
-            c[2][u] *= qw.z;
-            c[3][u] *= qw.w;
+                for (int col = 0; col < 8; ++col) v[j][col] = (sample4(pix, j, col) - 128) * (1 << kP);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) loeffler8_fwd(v[j]);
+
+            // the samples wait for the SSE in this lane's slot (the two 16-byte
+            // halves swap on every fourth lane: no bank conflicts)
+            if (MODE & kSse) park_rows(park, psw, pix);
+
+            // transpose: rows 4h..4h+3 out, columns 4h..4h+3 in
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                sts128(xw + j * 32, v[j][0], v[j][1], v[j][2], v[j][3]);
+                sts128(xw + j * 32 + 16, v[j][4], v[j][5], v[j][6], v[j][7]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int4 t = lds128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32);
+                c[0][r] = t.x;
+                c[1][r] = t.y;
+                c[2][r] = t.z;
+                c[3][r] = t.w;
+            }
+
+            // column pass: c[i][u] = Y[u][4h + i]
+#pragma unroll
+            for (int i = 0; i < 4; ++i) loeffler8_fwd(c[i]);
+
+            // quantiser: high word of Y M + 2^31, with - [Y < 0] at the tie
+            // entries (u, v in {0, 4}: i = 0 and u = 0 or 4 in both lanes)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int4 m = *reinterpret_cast<const int4*>(Mh + u * 8);
+                const int mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int y = c[i][u];
+                    long long p = (long long)y * (long long)mv[i] + 0x80000000ll;
+                    if (tie_entry(u, i)) p += (long long)(y >> 31);
+                    c[i][u] = (int)(p >> 32);
+                }
+            }
+
+            // coefficients: row u of the block is 16 bytes, lane h writes its half
+            if ((MODE & kStoreCoef) && active) {
+                uint2* g = reinterpret_cast<uint2*>(P.coef + (size_t)(b0 + k) * 64 + 4 * h);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    g[2 * u] = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
+                                          ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
+            }
+            if (!(MODE & kInverse)) continue;   // forward pass only
+
+            // dequantiser G = q (Q W): the clamp of the definition never acts
+            // on this kernel's own codes (|q Q| < 1200)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
+                c[0][u] *= qw.x;
+                c[1][u] *= qw.y;
+                c[2][u] *= qw.z;
+                c[3][u] *= qw.w;
+            }
+        } else {
+            // coefficients in: lane h reads the 8-byte half of each row u; the
+            // SSE reference rows wait in its slot
+            if (active) {
+                const uint2* g = reinterpret_cast<const uint2*>(P.coef + (size_t)(b0 + k) * 64 + 4 * h);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint2 w = __ldg(g + 2 * u);
+                    c[0][u] = (int)(int16_t)(w.x & 0xFFFFu);
+                    c[1][u] = (int)w.x >> 16;
+                    c[2][u] = (int)(int16_t)(w.y & 0xFFFFu);
+                    c[3][u] = (int)w.y >> 16;
+                }
+                if (MODE & kSse) {
+                    load_rows4(P.ref, P.ref_pitch, P.width, P.height, by, bx, h, (P.flags & kVecRef) != 0, pix);
+                    park_rows(park, psw, pix);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) c[0][u] = c[1][u] = c[2][u] = c[3][u] = 0;
+            }
+            // dequantiser G = clamp(q Q, -4096, 4096) W for arbitrary codes
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int4 q4 = *reinterpret_cast<const int4*>(Qh + u * 8);
+                const int4 w4 = *reinterpret_cast<const int4*>(Wh + u * 8);
+                c[0][u] = max(-kDequantClamp, min(kDequantClamp, c[0][u] * q4.x)) * w4.x;
+                c[1][u] = max(-kDequantClamp, min(kDequantClamp, c[1][u] * q4.y)) * w4.y;
+                c[2][u] = max(-kDequantClamp, min(kDequantClamp, c[2][u] * q4.z)) * w4.z;
+                c[3][u] = max(-kDequantClamp, min(kDequantClamp, c[3][u] * q4.w)) * w4.w;
+            }
         }
         c[0][0] += dc_bias;
 
@@ -260,12 +312,7 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
             store_rows4(P.dst, P.dst_pitch, P.width, P.height, by, bx, h, (P.flags & kVecDst) != 0, out);
 
         if ((MODE & kSse) && active) {
-            {
-                const uint4 a = *reinterpret_cast<const uint4*>(park + 16 * psw);
-                const uint4 b = *reinterpret_cast<const uint4*>(park + 16 * (psw ^ 1));
-                pix[0][0] = a.x; pix[0][1] = a.y; pix[1][0] = a.z; pix[1][1] = a.w;
-                pix[2][0] = b.x; pix[2][1] = b.y; pix[3][0] = b.z; pix[3][1] = b.w;
-            }
+            unpark_rows(park, psw, pix);
             const int nr = min(4, P.height - (by * 8 + 4 * h)), nc = min(8, P.width - bx * 8);
             if (nr == 4 && nc == 8) {
 #pragma unroll
@@ -285,6 +332,59 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
         }
     }
     return (MODE & kSse) ? warp_sum(e) : 0u;
+}
+
+// Direct (non-batched) fused calls with two lanes per block: grid-stride over
+// the warp tiles of up to kMaxPlanes planes, tables in shared memory, SSE
+// summed per CTA and added to each plane's word once (zero on entry).
+constexpr int kPairCodecHeader = 2 * (int)sizeof(QuantSet) + kMaxPlanes * 8;
+static_assert(kPairCodecHeader % 16 == 0, "per-warp buffers must stay 16-byte aligned");
+
+__host__ __device__ constexpr int pair_codec_smem_bytes(int threads) {
+    return kPairCodecHeader + (threads / 32) * (kXBytes + kParkBytes);
+}
+
+template <unsigned MODE>
+__global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_codec_pair(const __grid_constant__ DirectArgs args) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    QuantSet* tabs = reinterpret_cast<QuantSet*>(smem);
+    unsigned long long* csse = reinterpret_cast<unsigned long long*>(smem + 2 * sizeof(QuantSet));
+    {
+        const uint32_t* s = reinterpret_cast<const uint32_t*>(args.tabs);
+        uint32_t* d = reinterpret_cast<uint32_t*>(tabs);
+        for (int i = threadIdx.x; i < (int)(2 * sizeof(QuantSet) / 4); i += blockDim.x) d[i] = s[i];
+        if (threadIdx.x < kMaxPlanes) csse[threadIdx.x] = 0ull;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int warps_per_cta = blockDim.x >> 5;
+    uint8_t* xb = smem + kPairCodecHeader + warp * (kXBytes + kParkBytes);
+    for (int tile = blockIdx.x * warps_per_cta + warp; tile < args.ntiles; tile += gridDim.x * warps_per_cta) {
+        int pi = 0;
+#pragma unroll
+        for (int k = 1; k < kMaxPlanes; ++k)
+            if (k < args.nplanes && tile >= args.p[k].tile_begin) pi = k;
+        const PlaneArg& P = args.p[pi];
+        const unsigned e = process_tile_pair<MODE>(P, tabs[P.table], tile - P.tile_begin, lane, xb);
+        if ((MODE & kSse) && lane == 0 && e) atomicAdd(&csse[pi], (unsigned long long)e);
+    }
+    __syncthreads();
+    if ((MODE & kSse) && threadIdx.x < args.nplanes && csse[threadIdx.x])
+        atomicAdd(args.p[threadIdx.x].sse, csse[threadIdx.x]);
+}
+
+// Host launcher of k_codec_pair: one persistent grid of resident CTAs.
+template <unsigned MODE>
+inline cudaError_t launch_codec_pair(const DirectArgs& a, int num_sms, int threads, cudaStream_t s) {
+    const size_t smem = pair_codec_smem_bytes(threads);
+    cudaError_t e = cudaFuncSetAttribute(k_codec_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_codec_pair<MODE>, threads, smem);
+    if (e != cudaSuccess) return e;
+    k_codec_pair<MODE><<<persistent_grid(a.ntiles, threads, num_sms, occ), threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace dctgb

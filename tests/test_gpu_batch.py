@@ -261,3 +261,23 @@ def test_batch_maximum_plane_sampled(D, lanes):
         d = rec[r0:r0 + 4096].to(torch.int32) - src[r0:r0 + 4096].to(torch.int32)
         tot += int((d * d).sum(dtype=torch.int64))
     assert int(sse[0]) == tot
+
+
+def test_batch_sse_accumulators_reset_between_batches(D):
+    """The graph's SSE kernel accumulates into plan-owned words that its last
+    CTA writes out and zeroes: replays, a re-prepare with fewer items, an
+    autotune and a one-lane shape on the same plan all give the oracle's SSE."""
+    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    items_a = make_items(10, seed=21)
+    items_b = make_items(4, seed=22)
+    with D.Plan(512, 512, max_batch=16) as plan:
+        _, _, sse, _, _ = run_batch(D, plan, items_a, C | R | S, launches=3)
+        assert [int(v) for v in sse.cpu()] == [oracle(it)[2] for it in items_a]
+        for shape in (None, (64, 4, 32, 1), (256, 2, 32, 2)):
+            _, _, sse, _, _ = run_batch(D, plan, items_b, S, shape=shape, launches=2)
+            assert [int(v) for v in sse.cpu()] == [oracle(it)[2] for it in items_b], shape
+        D.dct_autotune(plan)
+        sse.fill_(-1)
+        D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+        assert [int(v) for v in sse.cpu()] == [oracle(it)[2] for it in items_b]
