@@ -248,18 +248,15 @@ typedef struct {
 } dct_launch_shape;
 
 /* Uploads a work list of n items (1..max_batch) to the plan's workspace,
- * builds the per-item tables and captures the persistent kernel(s) into a
- * CUDA graph on a plan-owned stream.  ops is a mask of DCT_OP_*:
+ * builds the per-item tables and captures [clear SSE, persistent kernel(s)]
+ * into a CUDA graph on a plan-owned stream.  ops is a mask of DCT_OP_*:
  *   COMPRESS alone                forward pass, coefficients written;
  *   RECONSTRUCT without COMPRESS  inverse pass from the items' coefficients;
  *   COMPRESS|RECONSTRUCT          one fused pass writing both;
  *   ... | TWO_PASS                forward kernel, then inverse kernel;
  *   SSE                           adds the SSE against src (alone: a fused
  *                                 pass that stores nothing).
- * With DCT_OP_SSE, sse_out (device uint64[n]) receives each item's SSE:
- * the kernel adds into plan-owned accumulators and its last CTA to finish
- * writes sse_out and zeroes them, so no clearing launch precedes it, and
- * launches of one plan's batch must not overlap on the GPU.
+ * With DCT_OP_SSE, sse_out (device uint64[n]) receives each item's SSE.
  * The call synchronises `stream` (the upload uses plan-owned pinned
  * staging buffers).  The device pointers
  * of the items are kept by the plan and used by every dct_batch_launch until

@@ -24,30 +24,7 @@ struct BatchArgs {
     const QuantSet* tabs;       // unique tables
     int32_t nitems;
     int32_t ntiles;
-    // Optional SSE finalisation without a clearing launch: when acc is set,
-    // warps add into acc[item] (zero on entry) instead of the item's SSE word,
-    // and the last CTA to finish (ticket) moves acc into the SSE words and
-    // zeroes acc and the ticket for the next launch.  When null, the SSE
-    // words themselves must be zero on entry.
-    unsigned long long* acc;
-    unsigned int* ticket;
 };
-
-// Last-CTA finalisation of BatchArgs::acc.  Every thread fences its own
-// atomics first, so once the ticket counts gridDim.x - 1 earlier CTAs all of
-// their additions are visible.  No thread waits on another CTA.
-__device__ __forceinline__ void finalize_sse(const BatchArgs& a) {
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        for (int i = threadIdx.x; i < a.nitems; i += blockDim.x) *a.items[i].sse = atomicExch(a.acc + i, 0ull);
-        if (threadIdx.x == 0) atomicExch(a.ticket, 0u);
-    }
-}
 
 __device__ __forceinline__ int find_item(const int32_t* __restrict__ tb, int n, int tile) {
     int lo = 0, hi = n - 1;   // largest i with tb[i] <= tile
@@ -120,7 +97,7 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
             cur = find_item(args.tile_begin, args.nitems, tile);
             item_end = __ldg(args.tile_begin + cur + 1);
             const PlaneArg* gi = args.items + cur;
-            item_sse = args.acc ? args.acc + cur : gi->sse;
+            item_sse = gi->sse;
             if (lane < (int)(sizeof(PlaneArg) / 4))
                 reinterpret_cast<uint32_t*>(&P)[lane] = __ldg(reinterpret_cast<const uint32_t*>(gi) + lane);
             const uint4* s = reinterpret_cast<const uint4*>(args.tabs + __ldg(&gi->table));
@@ -157,7 +134,6 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
         __syncwarp();
         flush_stats(wst, P.stats, lane);
     }
-    if ((MODE & kSse) && args.acc) finalize_sse(args);
 }
 
 // The fused modes with two lanes per 8x8 block (kernels_pair.cuh): the same
@@ -193,7 +169,7 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __gri
             cur = find_item(args.tile_begin, args.nitems, tile);
             item_end = __ldg(args.tile_begin + cur + 1);
             const PlaneArg* gi = args.items + cur;
-            item_sse = args.acc ? args.acc + cur : gi->sse;
+            item_sse = gi->sse;
             if (lane < (int)(sizeof(PlaneArg) / 4))
                 reinterpret_cast<uint32_t*>(&P)[lane] = __ldg(reinterpret_cast<const uint32_t*>(gi) + lane);
             const uint4* s = reinterpret_cast<const uint4*>(args.tabs + __ldg(&gi->table));
@@ -204,7 +180,6 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __gri
         sse += process_tile_pair<MODE>(P, *T, tile - P.tile_begin, lane, xb);
     }
     if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
-    if ((MODE & kSse) && args.acc) finalize_sse(args);
 }
 
 // Clears the SSE words (and statistics, with min words set to all ones).
@@ -276,8 +251,6 @@ struct BatchState {
     int32_t* d_tile_begin = nullptr;
     QuantSet* d_tabs = nullptr;
     unsigned long long* d_stats = nullptr;   // only for the rate-control helpers
-    unsigned long long* d_acc = nullptr;     // SSE accumulators (zero between launches)
-    unsigned int* d_ticket = nullptr;        // CTAs finished in the running launch (zero between launches)
     int cap = 0;
     // host staging (pinned)
     PlaneArg* h_items = nullptr;
@@ -287,6 +260,7 @@ struct BatchState {
     int n = 0, ntiles = 0, ntabs = 0;
     unsigned modes[2] = {0u, 0u};   // one or two kernels (two-pass)
     int nkernels = 0;
+    bool stats = false;
     bool sse = false;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -301,8 +275,6 @@ static void release(BatchState* b) {
     cudaFree(b->d_items);
     cudaFree(b->d_tile_begin);
     cudaFree(b->d_tabs);
-    cudaFree(b->d_acc);
-    cudaFree(b->d_ticket);
     cudaFreeHost(b->h_items);
     cudaFreeHost(b->h_tile_begin);
     cudaFreeHost(b->h_tabs);
@@ -320,8 +292,6 @@ static dct_status ensure_state(dct_plan_t plan) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(PlaneArg) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int32_t) * (cap + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tabs, sizeof(QuantSet) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_acc, sizeof(unsigned long long) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(PlaneArg) * cap);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tile_begin, sizeof(int32_t) * (cap + 1));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tabs, sizeof(QuantSet) * cap);
@@ -354,7 +324,7 @@ static int batch_grid(const dct_plan_s* plan, unsigned mode, const dct_launch_sh
     return std::min(need, plan->num_sms * per_sm);
 }
 
-// Records the kernel(s) on the capture stream and instantiates the graph.
+// Records [init, kernel(s)] on the capture stream and instantiates the graph.
 static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     BatchState* b = plan->batch;
     if (b->exec) {
@@ -364,16 +334,16 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     cudaStream_t s = b->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    // The SSE words need no clearing launch: the SSE kernel accumulates into
-    // the plan's zeroed accumulators and its last CTA writes them out.
+    if (b->sse || b->stats) {
+        const int g = std::min(1024, (b->n + 255) / 256);
+        k_batch_init<<<g, 256, 0, s>>>(b->d_items, b->n, b->sse ? 1 : 0, b->stats ? 1 : 0);
+    }
     BatchArgs a;
     a.items = b->d_items;
     a.tile_begin = b->d_tile_begin;
     a.tabs = b->d_tabs;
     a.nitems = b->n;
     a.ntiles = b->ntiles;
-    a.acc = b->sse ? b->d_acc : nullptr;
-    a.ticket = b->sse ? b->d_ticket : nullptr;
     for (int k = 0; k < b->nkernels; ++k) {
         KernelPtr kp = batch_kernel(b->modes[k], sh);
         const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k], sh);
@@ -416,8 +386,6 @@ cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* ti
     a.tabs = tabs;
     a.nitems = nitems;
     a.ntiles = ntiles;
-    a.acc = nullptr;
-    a.ticket = nullptr;
     kp<<<batch_grid(plan, mode, sh, ntiles), sh.threads_per_cta, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -531,6 +499,7 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
         b->modes[0] = mode;
         b->nkernels = 1;
     }
+    b->stats = false;
     b->sse = sse;
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -538,9 +507,6 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_tile_begin, b->h_tile_begin, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tabs, b->h_tabs, sizeof(QuantSet) * ntabs, cudaMemcpyHostToDevice, s);
-    // every launch leaves the accumulators and the ticket at zero; start there
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_acc, 0, sizeof(unsigned long long) * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // staging buffers are reused by the next prepare
     if (e != cudaSuccess) return cuda_fail(e, "batch upload");
 

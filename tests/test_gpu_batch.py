@@ -263,10 +263,10 @@ def test_batch_maximum_plane_sampled(D, lanes):
     assert int(sse[0]) == tot
 
 
-def test_batch_sse_accumulators_reset_between_batches(D):
-    """The graph's SSE kernel accumulates into plan-owned words that its last
-    CTA writes out and zeroes: replays, a re-prepare with fewer items, an
-    autotune and a one-lane shape on the same plan all give the oracle's SSE."""
+def test_batch_sse_restarts_between_batches(D):
+    """Every replay starts the SSE words from zero: replays, a re-prepare
+    with fewer items, other launch shapes and an autotune on the same plan
+    all give the oracle's SSE."""
     C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
     items_a = make_items(10, seed=21)
     items_b = make_items(4, seed=22)
