@@ -13,6 +13,12 @@ category(v) = number of bits of |v| (0 for v = 0).  With the symbol counts
 n_s (DC and AC separately, N = sum n_s) the plane costs
   bits = amplitude bits + sum_s n_s log2(N / n_s)
 which is what an ideal static code for that plane's own statistics spends.
+An achievable count: the plane's DC symbols and its AC symbols each get an
+optimal prefix code whose codewords are at most 16 bits long (the limit of
+JPEG's Huffman tables), found by the package-merge method of Larmore and
+Hirschberg; the plane then costs
+  bits = amplitude bits + sum_s n_s len_s(DC) + sum_s n_s len_s(AC)
+with a lone symbol coded in one bit.
 
 Test infrastructure only (see the package docstring).
 """
@@ -79,3 +85,60 @@ def entropy_bits(hist):
 def plane_bits(coeffs):
     dc, ac, amp, _ = plane_histograms(coeffs)
     return amp + entropy_bits(dc) + entropy_bits(ac)
+
+
+def limited_code_lengths(counts, max_len=16):
+    """Codeword lengths of an optimal prefix code over the symbols with
+    non-zero counts, no codeword longer than max_len (package-merge).
+    Returns a list aligned with ``counts`` (0 for absent symbols)."""
+    live = [i for i, c in enumerate(counts) if c > 0]
+    lengths = [0] * len(counts)
+    if not live:
+        return lengths
+    if len(live) == 1:
+        lengths[live[0]] = 1
+        return lengths
+    if len(live) > (1 << max_len):
+        raise ValueError("too many symbols for the length limit")
+    # An item is (weight, per-leaf multiplicity).  The leaves, sorted by
+    # weight (ties by symbol index), seed every level; level by level the
+    # sorted list is packaged in adjacent pairs and merged with the leaves.
+    leaves = sorted(((counts[i], i) for i in live))
+    leaf_items = [(w, {i: 1}) for w, i in leaves]
+
+    def merge(a, b):
+        out, x, y = [], 0, 0
+        while x < len(a) or y < len(b):
+            if y == len(b) or (x < len(a) and a[x][0] <= b[y][0]):
+                out.append(a[x])
+                x += 1
+            else:
+                out.append(b[y])
+                y += 1
+        return out
+
+    current = list(leaf_items)
+    for _ in range(max_len - 1):
+        packages = []
+        for k in range(0, len(current) - 1, 2):
+            wa, ma = current[k]
+            wb, mb = current[k + 1]
+            m = dict(ma)
+            for key, v in mb.items():
+                m[key] = m.get(key, 0) + v
+            packages.append((wa + wb, m))
+        current = merge(leaf_items, packages)
+    for _, m in current[:2 * len(live) - 2]:
+        for key, v in m.items():
+            lengths[key] += v
+    return lengths
+
+
+def code_cost(counts, max_len=16):
+    """Bits of the symbols under limited_code_lengths."""
+    return sum(c * l for c, l in zip(counts, limited_code_lengths(counts, max_len)))
+
+
+def plane_huffman_bits(coeffs):
+    dc, ac, amp, _ = plane_histograms(coeffs)
+    return amp + code_cost(dc) + code_cost(ac)

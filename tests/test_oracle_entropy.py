@@ -40,3 +40,88 @@ def test_entropy_bits_closed_forms():
     assert entropy.entropy_bits([4, 4]) == 8.0
     assert entropy.entropy_bits([7]) == 0.0
     assert abs(entropy.entropy_bits([1, 3]) - (2 + 3 * math.log2(4 / 3))) < 1e-12
+
+
+# ---- optimal length-limited prefix code (package-merge) -------------------
+
+import heapq
+import itertools
+
+
+def huffman_cost(counts):
+    """Plain Huffman (no length limit), merging the two lightest subtrees:
+    the cost is the sum of the merged weights."""
+    h = [c for c in counts if c > 0]
+    if len(h) < 2:
+        return sum(h)
+    heapq.heapify(h)
+    cost = 0
+    while len(h) > 1:
+        a, b = heapq.heappop(h), heapq.heappop(h)
+        cost += a + b
+        heapq.heappush(h, a + b)
+    return cost
+
+
+def huffman_depth(counts):
+    h = [(c, 0) for c in counts if c > 0]
+    heapq.heapify(h)
+    while len(h) > 1:
+        (a, da), (b, db) = heapq.heappop(h), heapq.heappop(h)
+        heapq.heappush(h, (a + b, max(da, db) + 1))
+    return h[0][1]
+
+
+def brute_force_cost(counts, max_len):
+    w = [c for c in counts if c > 0]
+    best = None
+    for ls in itertools.product(range(1, max_len + 1), repeat=len(w)):
+        if sum(2.0 ** -l for l in ls) <= 1.0:
+            c = sum(a * b for a, b in zip(w, ls))
+            best = c if best is None else min(best, c)
+    return best
+
+
+def test_code_lengths_closed_forms():
+    assert entropy.limited_code_lengths([1, 1, 2, 4]) == [3, 3, 2, 1]
+    assert entropy.limited_code_lengths([0, 9, 0]) == [0, 1, 0]
+    assert entropy.limited_code_lengths([5, 0, 3]) == [1, 0, 1]
+    assert entropy.limited_code_lengths([0, 0]) == [0, 0]
+    assert entropy.limited_code_lengths([1] * 8) == [3] * 8
+
+
+def test_code_matches_brute_force_on_small_alphabets():
+    rng = np.random.default_rng(7)
+    for n in range(2, 7):
+        for max_len in (n - 1, 3, 4):
+            if (1 << max_len) < n:
+                continue
+            for _ in range(6):
+                c = [int(v) for v in rng.integers(1, 60, size=n)]
+                if _ == 0:
+                    c = [2 ** k for k in range(n)]      # skewed: the limit binds
+                assert entropy.code_cost(c, max_len) == brute_force_cost(c, max_len), (c, max_len)
+
+
+def test_code_equals_huffman_when_the_limit_is_slack():
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        c = [int(v) for v in rng.integers(200, 5000, size=256)]
+        c[rng.integers(0, 256)] = 0
+        assert huffman_depth(c) <= 16
+        assert entropy.code_cost(c) == huffman_cost(c)
+        ls = entropy.limited_code_lengths(c)
+        assert sum(2.0 ** -l for l in ls if l) == 1.0
+
+
+def test_code_limit_binds_on_fibonacci_weights():
+    fib = [1, 1]
+    while len(fib) < 24:
+        fib.append(fib[-1] + fib[-2])
+    assert huffman_depth(fib) == 23
+    ls = entropy.limited_code_lengths(fib)
+    assert max(ls) == 16 and sum(2.0 ** -l for l in ls) == 1.0
+    assert entropy.code_cost(fib) > huffman_cost(fib)
+    # within the entropy bound of any prefix code
+    n = sum(fib)
+    assert entropy.code_cost(fib) >= entropy.entropy_bits(fib) - 1e-9 * n
