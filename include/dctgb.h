@@ -196,6 +196,13 @@ dct_status dct_entropy_stats(dct_plan_t plan, const int16_t* coeffs, const dct_p
  * ideal static code for the plane's own symbol statistics). */
 double dct_entropy_bits(const uint64_t* stats_host);
 
+/* Host only: an achievable bit count of one plane from the same words:
+ * amplitude bits + the cost of an optimal prefix code for the DC counts and
+ * one for the AC counts, no codeword longer than 16 bits (the limit of
+ * JPEG's Huffman tables; package-merge), a lone symbol coded in one bit.
+ * 0 for a NULL pointer. */
+uint64_t dct_huffman_bits(const uint64_t* stats_host);
+
 /* SSE and PSNR of two sets of planes of equal sizes (Eq. 23, Eq. 24).
  *  sse_out    device uint64[nplanes], overwritten.
  *  psnr_host  optional host double[nplanes + 1]: per-plane PSNR and the

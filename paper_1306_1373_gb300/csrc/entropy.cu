@@ -7,14 +7,17 @@
 //   amplitude bits: the category of every coded value
 // One lane reads one block's 64 stored int16 coefficients; symbol counts
 // go to per-CTA shared histograms (one per plane) flushed once per CTA.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "host_common.h"
 
 namespace dctgb {
 
 constexpr int kEntWords = DCT_ENTROPY_WORDS;   // 16 DC + 256 AC + amplitude bits + blocks
+constexpr int kMaxCodeLen = 16;                 // longest codeword of the prefix codes (as JPEG's Huffman tables)
 
 // Natural index u*8+v of zig-zag position k (T.81 Figure A.6): diagonals
 // s = u + v in turn, odd s with u rising, even s with u falling.  Called with
@@ -162,6 +165,87 @@ extern "C" double dct_entropy_bits(const uint64_t* stats_host) {
         for (int i = lo; i < hi; ++i) n += (double)stats_host[i];
         for (int i = lo; i < hi; ++i)
             if (stats_host[i]) bits += (double)stats_host[i] * std::log2(n / (double)stats_host[i]);
+    }
+    return bits;
+}
+
+namespace dctgb {
+
+// Codeword lengths of an optimal prefix code over the symbols with non-zero
+// counts, none longer than max_len bits: package-merge (Larmore and
+// Hirschberg).  Every level lists the leaves (sorted by count, then symbol)
+// merged with the adjacent pairs of the previous level's list, leaves first
+// on equal weights; a symbol's length is the number of times its leaf occurs
+// among the first 2m - 2 items of the last level (m live symbols).  A lone
+// symbol gets one bit.
+static void limited_code_lengths(const uint64_t* counts, int n, int max_len, int* len) {
+    struct Node {
+        uint64_t w;
+        int sym;      // leaf symbol, or -1 for a package
+        int a, b;     // children of a package
+    };
+    std::vector<Node> nodes;
+    std::vector<int> leaves;
+    for (int i = 0; i < n; ++i) {
+        len[i] = 0;
+        if (counts[i]) {
+            nodes.push_back(Node{counts[i], i, -1, -1});
+            leaves.push_back((int)nodes.size() - 1);
+        }
+    }
+    const int m = (int)leaves.size();
+    if (m == 0) return;
+    if (m == 1) {
+        len[nodes[leaves[0]].sym] = 1;
+        return;
+    }
+    std::sort(leaves.begin(), leaves.end(), [&](int x, int y) {
+        return nodes[x].w != nodes[y].w ? nodes[x].w < nodes[y].w : nodes[x].sym < nodes[y].sym;
+    });
+    std::vector<int> cur = leaves, next, packages;
+    for (int level = 1; level < max_len; ++level) {
+        packages.clear();
+        for (size_t k = 0; k + 1 < cur.size(); k += 2) {
+            nodes.push_back(Node{nodes[cur[k]].w + nodes[cur[k + 1]].w, -1, cur[k], cur[k + 1]});
+            packages.push_back((int)nodes.size() - 1);
+        }
+        next.clear();
+        size_t x = 0, y = 0;
+        while (x < leaves.size() || y < packages.size()) {
+            if (y == packages.size() || (x < leaves.size() && nodes[leaves[x]].w <= nodes[packages[y]].w))
+                next.push_back(leaves[x++]);
+            else
+                next.push_back(packages[y++]);
+        }
+        cur.swap(next);
+    }
+    std::vector<int> stack;
+    for (int k = 0; k < 2 * m - 2; ++k) {
+        stack.push_back(cur[k]);
+        while (!stack.empty()) {
+            const Node& nd = nodes[stack.back()];
+            stack.pop_back();
+            if (nd.sym >= 0) {
+                ++len[nd.sym];
+            } else {
+                stack.push_back(nd.a);
+                stack.push_back(nd.b);
+            }
+        }
+    }
+}
+
+}  // namespace dctgb
+
+extern "C" uint64_t dct_huffman_bits(const uint64_t* stats_host) {
+    using namespace dctgb;
+    if (!stats_host) return 0;
+    uint64_t bits = stats_host[272];
+    int len[256];
+    for (int part = 0; part < 2; ++part) {
+        const int lo = part ? 16 : 0, n = part ? 256 : 16;
+        limited_code_lengths(stats_host + lo, n, kMaxCodeLen, len);
+        for (int i = 0; i < n; ++i) bits += stats_host[lo + i] * (uint64_t)len[i];
     }
     return bits;
 }

@@ -99,6 +99,7 @@ _SIGNATURES = {
                                          ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), _P]),
     "dct_entropy_stats": (ctypes.c_int, [_P, _P, ctypes.POINTER(dct_plane), ctypes.c_int, _P, _P]),
     "dct_entropy_bits": (ctypes.c_double, [ctypes.POINTER(ctypes.c_uint64)]),
+    "dct_huffman_bits": (ctypes.c_uint64, [ctypes.POINTER(ctypes.c_uint64)]),
     "dct_psnr": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), ctypes.c_int, _P,
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "dct_psnr_from_sse": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]),
@@ -374,6 +375,13 @@ def dct_entropy_bits(stats_row):
     """Bits of one plane from its 274 statistics words (host)."""
     a = np.ascontiguousarray(np.asarray(stats_row, dtype=np.uint64))
     return load().dct_entropy_bits(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+
+
+def dct_huffman_bits(stats_row):
+    """Achievable bits of one plane (16-bit length-limited optimal prefix
+    codes for its DC and AC symbols) from its 274 statistics words (host)."""
+    a = np.ascontiguousarray(np.asarray(stats_row, dtype=np.uint64))
+    return int(load().dct_huffman_bits(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
 
 
 def dct_psnr(plan, a_planes, b_planes, max_value=0.0, sse=None, host=True, stream=None):

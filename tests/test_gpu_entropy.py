@@ -30,6 +30,8 @@ def test_symbol_statistics_match_oracle(D, quality):
             assert st[:16].tolist() == dc and st[16:272].tolist() == ac
             assert int(st[272]) == amp and int(st[273]) == nb
             assert abs(D.dct_entropy_bits(st) - entropy.plane_bits(ref)) <= 1e-9 * max(1.0, entropy.plane_bits(ref))
+            assert D.dct_huffman_bits(st) == entropy.plane_huffman_bits(ref)
+            assert D.dct_huffman_bits(st) >= D.dct_entropy_bits(st) - 1e-6
 
 
 def test_yuv420_statistics_and_rate_falls_with_quality(D):

@@ -108,3 +108,28 @@ def test_product_path_does_not_import_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "oracle" not in text, fn
+
+
+def test_huffman_bits_host_function_matches_the_oracle():
+    """dct_huffman_bits is host code: it runs here on the symbol counts the
+    oracle produces for random coefficient planes and for hand-made counts
+    where the 16-bit limit binds."""
+    from oracle import entropy
+    from paper_1306_1373_gb300 import dctgb as D
+    rng = np.random.default_rng(11)
+    for trial in range(12):
+        nblk = int(rng.integers(1, 40))
+        scale = float(rng.choice([0.3, 2.0, 20.0]))
+        c = np.round(rng.laplace(0, scale, size=(nblk, 64)) * (rng.random((nblk, 64)) < 0.4)).astype(np.int64)
+        dc, ac, amp, nb = entropy.plane_histograms(c)
+        words = np.array(dc + ac + [amp, nb], dtype=np.uint64)
+        assert D.dct_huffman_bits(words) == entropy.plane_huffman_bits(c), trial
+    fib = [1, 1]
+    while len(fib) < 24:
+        fib.append(fib[-1] + fib[-2])
+    words = np.zeros(274, dtype=np.uint64)
+    words[16:16 + 24] = fib
+    words[0:3] = [5, 0, 7]
+    words[272] = 99
+    assert D.dct_huffman_bits(words) == 99 + entropy.code_cost([5, 0, 7]) + entropy.code_cost(fib)
+    assert D.dct_huffman_bits(np.zeros(274, dtype=np.uint64)) == 0
