@@ -3,11 +3,14 @@
 // shape chosen by timing candidates (dct_autotune).
 //
 // Work list: item i covers warp tiles [tile_begin[i], tile_begin[i+1]).
-// Each warp takes one contiguous range of tiles (ranges differ by at most one
-// tile), so consecutive tiles of a warp usually belong to the same item: the
-// warp keeps that item's descriptor and tables in registers / its own shared
-// memory slot and accumulates the item's SSE in a register, flushing it with
-// one atomic add when the item changes.
+// One-lane kernels: each warp takes one contiguous range of tiles (ranges
+// differ by at most one tile).  Two-lane kernels in the captured graph: each
+// warp claims its next tile from a counter the graph's first launch resets,
+// so warps that finish early keep working and the claimed tiles of a warp
+// only increase.  Either way consecutive tiles of a warp usually belong to
+// the same item: the warp keeps that item's descriptor and tables in its own
+// shared memory slot and accumulates the item's SSE in a register, flushing
+// it with one atomic add when the item changes.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -24,6 +27,10 @@ struct BatchArgs {
     const QuantSet* tabs;       // unique tables
     int32_t nitems;
     int32_t ntiles;
+    // Two-lane kernels: when set, warps claim tiles one at a time from this
+    // counter (zero on entry, reset by k_batch_init) instead of taking a
+    // fixed contiguous range; warps that finish early keep working.
+    unsigned int* next_tile;
 };
 
 __device__ __forceinline__ int find_item(const int32_t* __restrict__ tb, int n, int tile) {
@@ -136,10 +143,12 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
     }
 }
 
-// The fused modes with two lanes per 8x8 block (kernels_pair.cuh): the same
-// contiguous tile ranges and per-item descriptor/table slot as k_batch; the
-// samples are read straight from global memory (the 32 resident warps per SM
-// hide the latency that the one-lane kernel hides with cp.async prefetch).
+// The two-lane modes (kernels_pair.cuh): the same per-item descriptor/table
+// slot as k_batch, tiles claimed one at a time from args.next_tile (or the
+// same contiguous ranges as k_batch when it is null); the samples are read
+// straight from global memory (the 32 resident warps per SM hide the latency
+// that the one-lane kernel hides with cp.async prefetch).  Claimed tiles only
+// increase, so a warp still meets each item's tiles in order.
 template <unsigned MODE>
 __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __grid_constant__ BatchArgs args) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -152,16 +161,29 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __gri
     PlaneArg& P = *reinterpret_cast<PlaneArg*>(base + sizeof(QuantSet));
     uint8_t* xb = base + sizeof(QuantSet) + kDescBytes;
 
-    const long long total_warps = (long long)gridDim.x * warps_per_cta;
-    const long long gw = (long long)blockIdx.x * warps_per_cta + warp;
-    const int t_begin = (int)((gw * args.ntiles) / total_warps);
-    const int t_end = (int)(((gw + 1) * args.ntiles) / total_warps);
+    const bool claim = args.next_tile != nullptr;
+    int tile = 0, limit = 0;
+    if (!claim) {
+        const long long total_warps = (long long)gridDim.x * warps_per_cta;
+        const long long gw = (long long)blockIdx.x * warps_per_cta + warp;
+        tile = (int)((gw * args.ntiles) / total_warps);
+        limit = (int)(((gw + 1) * args.ntiles) / total_warps);
+    }
 
     int cur = -1;
     int item_end = 0;
     unsigned long long* item_sse = nullptr;
     unsigned long long sse = 0ull;
-    for (int tile = t_begin; tile < t_end; ++tile) {
+    for (;; ++tile) {
+        if (tile >= limit) {
+            if (!claim) break;
+            int t = 0;
+            if (lane == 0) t = (int)atomicAdd(args.next_tile, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= args.ntiles) break;
+            tile = t;
+            limit = t + 1;
+        }
         if (cur < 0 || tile >= item_end) {
             __syncwarp();
             if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
@@ -182,8 +204,11 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __gri
     if ((MODE & kSse) && cur >= 0 && lane == 0 && sse) atomicAdd(item_sse, sse);
 }
 
-// Clears the SSE words (and statistics, with min words set to all ones).
-__global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats) {
+// Clears the SSE words (and statistics, with min words set to all ones) and
+// the tile counters (may be null).
+__global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats,
+                             unsigned int* counters, int ncounters) {
+    if (counters && blockIdx.x == 0 && threadIdx.x < ncounters) counters[threadIdx.x] = 0u;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (do_sse) *items[i].sse = 0ull;
         if (do_stats) {
@@ -251,6 +276,7 @@ struct BatchState {
     int32_t* d_tile_begin = nullptr;
     QuantSet* d_tabs = nullptr;
     unsigned long long* d_stats = nullptr;   // only for the rate-control helpers
+    unsigned int* d_counters = nullptr;      // tile counters of the (up to two) captured kernels
     int cap = 0;
     // host staging (pinned)
     PlaneArg* h_items = nullptr;
@@ -275,6 +301,7 @@ static void release(BatchState* b) {
     cudaFree(b->d_items);
     cudaFree(b->d_tile_begin);
     cudaFree(b->d_tabs);
+    cudaFree(b->d_counters);
     cudaFreeHost(b->h_items);
     cudaFreeHost(b->h_tile_begin);
     cudaFreeHost(b->h_tabs);
@@ -292,6 +319,7 @@ static dct_status ensure_state(dct_plan_t plan) {
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(PlaneArg) * cap);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int32_t) * (cap + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tabs, sizeof(QuantSet) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(PlaneArg) * cap);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tile_begin, sizeof(int32_t) * (cap + 1));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tabs, sizeof(QuantSet) * cap);
@@ -334,9 +362,13 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     cudaStream_t s = b->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    if (b->sse || b->stats) {
-        const int g = std::min(1024, (b->n + 255) / 256);
-        k_batch_init<<<g, 256, 0, s>>>(b->d_items, b->n, b->sse ? 1 : 0, b->stats ? 1 : 0);
+    // one launch clears the SSE words and the two-lane kernels' tile counters
+    bool any_pair = false;
+    for (int k = 0; k < b->nkernels; ++k) any_pair = any_pair || use_pair(b->modes[k], sh);
+    if (b->sse || b->stats || any_pair) {
+        const int g = std::min(1024, std::max(1, (b->n + 255) / 256));
+        k_batch_init<<<g, 256, 0, s>>>(b->d_items, b->n, b->sse ? 1 : 0, b->stats ? 1 : 0,
+                                       any_pair ? b->d_counters : nullptr, 2);
     }
     BatchArgs a;
     a.items = b->d_items;
@@ -347,6 +379,7 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     for (int k = 0; k < b->nkernels; ++k) {
         KernelPtr kp = batch_kernel(b->modes[k], sh);
         const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k], sh);
+        a.next_tile = use_pair(b->modes[k], sh) ? b->d_counters + k : nullptr;
         cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kp<<<batch_grid(plan, b->modes[k], sh, b->ntiles), sh.threads_per_cta, smem, s>>>(a);
     }
@@ -386,6 +419,7 @@ cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* ti
     a.tabs = tabs;
     a.nitems = nitems;
     a.ntiles = ntiles;
+    a.next_tile = nullptr;   // fixed contiguous ranges: no counter to reset
     kp<<<batch_grid(plan, mode, sh, ntiles), sh.threads_per_cta, smem, s>>>(a);
     return cudaGetLastError();
 }

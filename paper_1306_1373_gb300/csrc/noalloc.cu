@@ -35,7 +35,8 @@ struct NoAllocList {
 static __device__ __align__(256) NoAllocList g_noalloc_list;
 
 // Kernels of batch.cu, launched unchanged.
-__global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats);
+__global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_sse, int do_stats,
+                             unsigned int* counters, int ncounters);
 
 constexpr int kMaxDevices = 64;
 static NoAllocList* g_list_addr[kMaxDevices];   // device address per device, nullptr until set up
@@ -166,7 +167,7 @@ extern "C" dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, 
         e = cudaMemcpyAsync(dlist->tile_begin, h.tile_begin, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "work list upload");
     if (sse) {
-        k_batch_init<<<1, 64, 0, s>>>(dlist->items, n, 1, 0);   // the SSE outputs start at zero
+        k_batch_init<<<1, 64, 0, s>>>(dlist->items, n, 1, 0, nullptr, 0);   // the SSE outputs start at zero
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "SSE clear launch");
     }
     if (two) {
