@@ -144,12 +144,13 @@ __global__ void __launch_bounds__(256, DCTGB_MINB) k_batch(const __grid_constant
 }
 
 // The two-lane modes (kernels_pair.cuh): the same per-item descriptor/table
-// slot as k_batch, tiles claimed one at a time from args.next_tile (or the
+// slot as k_batch, tiles claimed CHUNK at a time from args.next_tile (or the
 // same contiguous ranges as k_batch when it is null); the samples are read
 // straight from global memory (the 32 resident warps per SM hide the latency
 // that the one-lane kernel hides with cp.async prefetch).  Claimed tiles only
-// increase, so a warp still meets each item's tiles in order.
-template <unsigned MODE>
+// increase, so a warp still meets each item's tiles in order.  CHUNK > 1
+// spares the counter on large batches (many tiles per warp).
+template <unsigned MODE, int CHUNK>
 __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __grid_constant__ BatchArgs args) {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int kWarpBytes = pair_warp_smem_bytes();
@@ -178,11 +179,11 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_batch_pair(const __gri
         if (tile >= limit) {
             if (!claim) break;
             int t = 0;
-            if (lane == 0) t = (int)atomicAdd(args.next_tile, 1u);
+            if (lane == 0) t = (int)atomicAdd(args.next_tile, (unsigned)CHUNK);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= args.ntiles) break;
             tile = t;
-            limit = t + 1;
+            limit = CHUNK == 1 ? t + 1 : min(t + CHUNK, args.ntiles);
         }
         if (cur < 0 || tile >= item_end) {
             __syncwarp();
@@ -224,21 +225,33 @@ __global__ void k_batch_init(const PlaneArg* __restrict__ items, int n, int do_s
 
 using KernelPtr = void (*)(BatchArgs);
 
-static KernelPtr pair_kernel(unsigned mode) {
+template <int C>
+static KernelPtr pair_kernel_c(unsigned mode) {
     switch (mode) {
-        case kLoadPix | kStoreCoef: return k_batch_pair<kLoadPix | kStoreCoef>;
-        case kLoadCoef | kInverse | kStoreRecon: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon>;
-        case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kSse>;
-        case kLoadPix | kInverse | kSse: return k_batch_pair<kLoadPix | kInverse | kSse>;
-        case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef>;
-        case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreRecon>;
+        case kLoadPix | kStoreCoef: return k_batch_pair<kLoadPix | kStoreCoef, C>;
+        case kLoadCoef | kInverse | kStoreRecon: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon, C>;
+        case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kSse, C>;
+        case kLoadPix | kInverse | kSse: return k_batch_pair<kLoadPix | kInverse | kSse, C>;
+        case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef, C>;
+        case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreRecon, C>;
         case kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon:
-            return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon>;
-        case kLoadPix | kInverse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kStoreRecon>;
+            return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef | kStoreRecon, C>;
+        case kLoadPix | kInverse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kStoreRecon, C>;
         case kLoadPix | kInverse | kStoreCoef | kStoreRecon:
-            return k_batch_pair<kLoadPix | kInverse | kStoreCoef | kStoreRecon>;
+            return k_batch_pair<kLoadPix | kInverse | kStoreCoef | kStoreRecon, C>;
         default: return nullptr;
     }
+}
+
+// Tiles a warp claims at a time: four once a launch has at least 16 tiles
+// per warp (the 512-image batch, about 60 per warp: 602 vs 577 GPix/s
+// measured), else one (the benchmark planes, about 8 per warp), so the last
+// claims still spread over all warps.
+constexpr int kClaimChunk = 4;
+constexpr int kChunkTilesPerWarp = 16;
+
+static KernelPtr pair_kernel(unsigned mode, bool chunked = false) {
+    return chunked ? pair_kernel_c<kClaimChunk>(mode) : pair_kernel_c<1>(mode);
 }
 
 // Two lanes per block when the shape asks for it and the mode has a two-lane
@@ -266,8 +279,8 @@ static KernelPtr one_lane_kernel(unsigned mode) {
     }
 }
 
-static KernelPtr batch_kernel(unsigned mode, const dct_launch_shape& sh) {
-    return use_pair(mode, sh) ? pair_kernel(mode) : one_lane_kernel(mode);
+static KernelPtr batch_kernel(unsigned mode, const dct_launch_shape& sh, bool chunked = false) {
+    return use_pair(mode, sh) ? pair_kernel(mode, chunked) : one_lane_kernel(mode);
 }
 
 struct BatchState {
@@ -377,11 +390,13 @@ static dct_status capture(dct_plan_t plan, const dct_launch_shape& sh) {
     a.nitems = b->n;
     a.ntiles = b->ntiles;
     for (int k = 0; k < b->nkernels; ++k) {
-        KernelPtr kp = batch_kernel(b->modes[k], sh);
+        const int grid = batch_grid(plan, b->modes[k], sh, b->ntiles);
+        const bool chunked = (long long)b->ntiles >= (long long)kChunkTilesPerWarp * grid * (sh.threads_per_cta / 32);
+        KernelPtr kp = batch_kernel(b->modes[k], sh, chunked);
         const size_t smem = batch_smem(sh.threads_per_cta, b->modes[k], sh);
         a.next_tile = use_pair(b->modes[k], sh) ? b->d_counters + k : nullptr;
         cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kp<<<batch_grid(plan, b->modes[k], sh, b->ntiles), sh.threads_per_cta, smem, s>>>(a);
+        kp<<<grid, sh.threads_per_cta, smem, s>>>(a);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaGetLastError();

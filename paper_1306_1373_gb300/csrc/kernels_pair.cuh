@@ -230,17 +230,17 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
                     g[2 * u] = make_uint2(((uint32_t)c[0][u] & 0xFFFFu) | ((uint32_t)c[1][u] << 16),
                                           ((uint32_t)c[2][u] & 0xFFFFu) | ((uint32_t)c[3][u] << 16));
             }
-            if (!(MODE & kInverse)) continue;   // forward pass only
-
             // dequantiser G = q (Q W): the clamp of the definition never acts
             // on this kernel's own codes (|q Q| < 1200)
+            if (MODE & kInverse) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
-                c[0][u] *= qw.x;
-                c[1][u] *= qw.y;
-                c[2][u] *= qw.z;
-                c[3][u] *= qw.w;
+                for (int u = 0; u < 8; ++u) {
+                    const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
+                    c[0][u] *= qw.x;
+                    c[1][u] *= qw.y;
+                    c[2][u] *= qw.z;
+                    c[3][u] *= qw.w;
+                }
             }
         } else {
             // coefficients in: lane h reads the 8-byte half of each row u; the
@@ -274,60 +274,63 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
                 c[3][u] = max(-kDequantClamp, min(kDequantClamp, c[3][u] * q4.w)) * w4.w;
             }
         }
-        c[0][0] += dc_bias;
+        if constexpr ((MODE & kInverse) != 0) {
+            c[0][0] += dc_bias;
 
-        // inverse column pass, transpose back, inverse row pass
+            // inverse column pass, transpose back, inverse row pass
 #pragma unroll
-        for (int i = 0; i < 4; ++i) loeffler8_inv(c[i]);
-        __syncwarp();                                // transpose reads done
+            for (int i = 0; i < 4; ++i) loeffler8_inv(c[i]);
+            __syncwarp();                                // transpose reads done
 #pragma unroll
-        for (int r = 0; r < 8; ++r) sts128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32, c[0][r], c[1][r], c[2][r], c[3][r]);
-        __syncwarp();
+            for (int r = 0; r < 8; ++r)
+                sts128(xr + (r >> 2) * kXRowHalf + (r & 3) * 32, c[0][r], c[1][r], c[2][r], c[3][r]);
+            __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int4 a = lds128(xw + j * 32);
-            const int4 b = lds128(xw + j * 32 + 16);
-            v[j][0] = a.x; v[j][1] = a.y; v[j][2] = a.z; v[j][3] = a.w;
-            v[j][4] = b.x; v[j][5] = b.y; v[j][6] = b.z; v[j][7] = b.w;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) loeffler8_inv(v[j]);
-
-        // descale, clamp, pack
-        uint32_t out[4][2];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                uint32_t wd = 0;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int s = clamp_u8(v[j][4 * q + t] >> (kR + 3));
-                    wd |= (uint32_t)s << (8 * t);
-                }
-                out[j][q] = wd;
+            for (int j = 0; j < 4; ++j) {
+                const int4 a = lds128(xw + j * 32);
+                const int4 b = lds128(xw + j * 32 + 16);
+                v[j][0] = a.x; v[j][1] = a.y; v[j][2] = a.z; v[j][3] = a.w;
+                v[j][4] = b.x; v[j][5] = b.y; v[j][6] = b.z; v[j][7] = b.w;
             }
-        }
-        if ((MODE & kStoreRecon) && active)
-            store_rows4(P.dst, P.dst_pitch, P.width, P.height, by, bx, h, (P.flags & kVecDst) != 0, out);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) loeffler8_inv(v[j]);
 
-        if ((MODE & kSse) && active) {
-            unpark_rows(park, psw, pix);
-            const int nr = min(4, P.height - (by * 8 + 4 * h)), nc = min(8, P.width - bx * 8);
-            if (nr == 4 && nc == 8) {
+            // descale, clamp, pack
+            uint32_t out[4][2];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < 4; ++j) {
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const unsigned ad = __vabsdiffu4(out[j][q], pix[j][q]);
-                        e = __dp4a(ad, ad, e);
+                for (int q = 0; q < 2; ++q) {
+                    uint32_t wd = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int s = clamp_u8(v[j][4 * q + t] >> (kR + 3));
+                        wd |= (uint32_t)s << (8 * t);
                     }
-            } else {
-                for (int j = 0; j < nr; ++j)
-                    for (int cc = 0; cc < nc; ++cc) {
-                        const int d = sample4(out, j, cc) - sample4(pix, j, cc);
-                        e += d * d;
-                    }
+                    out[j][q] = wd;
+                }
+            }
+            if ((MODE & kStoreRecon) && active)
+                store_rows4(P.dst, P.dst_pitch, P.width, P.height, by, bx, h, (P.flags & kVecDst) != 0, out);
+
+            if ((MODE & kSse) && active) {
+                unpark_rows(park, psw, pix);
+                const int nr = min(4, P.height - (by * 8 + 4 * h)), nc = min(8, P.width - bx * 8);
+                if (nr == 4 && nc == 8) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const unsigned ad = __vabsdiffu4(out[j][q], pix[j][q]);
+                            e = __dp4a(ad, ad, e);
+                        }
+                } else {
+                    for (int j = 0; j < nr; ++j)
+                        for (int cc = 0; cc < nc; ++cc) {
+                            const int d = sample4(out, j, cc) - sample4(pix, j, cc);
+                            e += d * d;
+                        }
+                }
             }
         }
     }
