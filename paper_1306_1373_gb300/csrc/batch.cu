@@ -420,11 +420,14 @@ static bool valid_shape(const dct_launch_shape& sh) {
 }
 
 cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* tile_begin, const QuantSet* tabs,
-                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s) {
+                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s, unsigned int* tile_counter) {
     dct_launch_shape sh = plan->shape;
     if (!valid_shape(sh)) sh = default_shape();
-    KernelPtr kp = batch_kernel(mode, sh);
-    if (!kp) return cudaErrorInvalidValue;
+    if (!batch_kernel(mode, sh)) return cudaErrorInvalidValue;
+    const int grid = batch_grid(plan, mode, sh, ntiles);
+    const bool claim = tile_counter != nullptr && use_pair(mode, sh);
+    const bool chunked = claim && (long long)ntiles >= (long long)kChunkTilesPerWarp * grid * (sh.threads_per_cta / 32);
+    KernelPtr kp = batch_kernel(mode, sh, chunked);
     const size_t smem = batch_smem(sh.threads_per_cta, mode, sh);
     cudaError_t e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -434,8 +437,8 @@ cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* ti
     a.tabs = tabs;
     a.nitems = nitems;
     a.ntiles = ntiles;
-    a.next_tile = nullptr;   // fixed contiguous ranges: no counter to reset
-    kp<<<batch_grid(plan, mode, sh, ntiles), sh.threads_per_cta, smem, s>>>(a);
+    a.next_tile = claim ? tile_counter : nullptr;
+    kp<<<grid, sh.threads_per_cta, smem, s>>>(a);
     return cudaGetLastError();
 }
 

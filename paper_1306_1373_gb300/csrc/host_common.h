@@ -54,9 +54,12 @@ void fill_plane(PlaneArg& a, const dct_plane& p, int& tile_cursor);
 void batch_release(dct_plan_t plan);
 
 // Launches the batched persistent kernel of `mode` over a device work list
-// (no graph), with the plan's launch shape (batch.cu).
+// (no graph), with the plan's launch shape (batch.cu).  With tile_counter (a
+// device word the caller has zeroed on `s` before the launch) a two-lane
+// kernel claims its tiles from it; without, warps take fixed ranges.
 cudaError_t batch_launch(unsigned mode, const PlaneArg* items, const int32_t* tile_begin, const QuantSet* tabs,
-                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s);
+                         int nitems, int ntiles, const dct_plan_s* plan, cudaStream_t s,
+                         unsigned int* tile_counter = nullptr);
 
 // Frees the plan's rate-control workspace (ratecontrol.cu).
 void rc_release(dct_plan_t plan);

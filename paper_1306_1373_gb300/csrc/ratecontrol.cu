@@ -52,6 +52,7 @@ struct RcState {
     int32_t* d_hi = nullptr;
     int32_t* d_mid = nullptr;
     unsigned long long* d_fsse = nullptr;
+    unsigned int* d_counter = nullptr;   // tile counter of the SSE passes
     // pinned host staging
     unsigned long long* h_thr = nullptr;
     unsigned long long* h_blo = nullptr;
@@ -68,10 +69,12 @@ struct RcState {
 // ---------------------------------------------------------------------------
 
 // table index of every plane of a slot frame for that frame's quality; clears
-// the planes' SSE words
+// the planes' SSE words and the next pass's tile counter
 __global__ void k_rc_set_quality(PlaneArg* items, int nitems, int k, const int32_t* __restrict__ frame,
-                                 const int32_t* __restrict__ q_slot, const int32_t* __restrict__ q_global) {
+                                 const int32_t* __restrict__ q_slot, const int32_t* __restrict__ q_global,
+                                 unsigned int* tile_counter) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *tile_counter = 0u;
     if (i >= nitems) return;
     const int f = i / k;
     const int q = q_slot ? q_slot[f] : q_global[frame[f]];
@@ -157,7 +160,7 @@ static void release_rc(RcState* r) {
     free_list(r->luma);
     free_list(r->sub);
     void* dev[] = {r->d_item_sse, r->d_stats, r->d_feats, r->d_target, r->d_w, r->d_h, r->d_q, r->d_sse,
-                   r->d_fell, r->d_thr, r->d_blo, r->d_bhi, r->d_lo, r->d_hi, r->d_mid, r->d_fsse};
+                   r->d_fell, r->d_thr, r->d_blo, r->d_bhi, r->d_lo, r->d_hi, r->d_mid, r->d_fsse, r->d_counter};
     for (void* p : dev) cudaFree(p);
     void* host[] = {r->h_thr, r->h_blo, r->h_bhi, r->h_target, r->h_w, r->h_h, r->h_fell};
     for (void* p : host) cudaFreeHost(p);
@@ -208,6 +211,7 @@ static dct_status ensure_rc(dct_plan_t plan, cudaStream_t s) {
     if (e == cudaSuccess) e = dalloc(&r->d_hi, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_mid, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_fsse, cap);
+    if (e == cudaSuccess) e = dalloc(&r->d_counter, 1);
     if (e == cudaSuccess) e = halloc(&r->h_thr, cap);
     if (e == cudaSuccess) e = halloc(&r->h_blo, cap);
     if (e == cudaSuccess) e = halloc(&r->h_bhi, cap);
@@ -278,9 +282,10 @@ static dct_status run_bisection(dct_plan_t plan, RcState* r, WorkList& w, int k,
     k_bisect_init<<<blocks_for(n), 128, 0, s>>>(r->d_lo, r->d_hi, n);
     for (int step = 0; step < kBisectSteps; ++step) {
         k_bisect_mid<<<blocks_for(n), 128, 0, s>>>(r->d_lo, r->d_hi, r->d_mid, n);
-        k_rc_set_quality<<<blocks_for(w.nitems), 128, 0, s>>>(w.d_items, w.nitems, k, w.d_frame, r->d_mid, nullptr);
+        k_rc_set_quality<<<blocks_for(w.nitems), 128, 0, s>>>(w.d_items, w.nitems, k, w.d_frame, r->d_mid, nullptr,
+                                                              r->d_counter);
         cudaError_t e = batch_launch(kLoadPix | kInverse | kSse, w.d_items, w.d_tb, r->d_bank, w.nitems, w.ntiles,
-                                     plan, s);
+                                     plan, s, r->d_counter);
         if (e != cudaSuccess) return cuda_fail(e, "bisection pass");
         k_rc_frame_sse<<<blocks_for(n), 128, 0, s>>>(w.d_items, n, k, r->d_fsse);
         if (step + 1 < kBisectSteps)
@@ -402,9 +407,9 @@ dct_status dct_rate_control(dct_plan_t plan, const dct_plane* planes, int planes
             return cuda_fail(e, "network launch");
         if ((st = build_list(r, r->all, planes, k, all, false, s)) != DCT_OK) return st;
         k_rc_set_quality<<<blocks_for(r->all.nitems), 128, 0, s>>>(r->all.d_items, r->all.nitems, k, r->all.d_frame,
-                                                                   nullptr, r->d_q);
+                                                                   nullptr, r->d_q, r->d_counter);
         e = batch_launch(kLoadPix | kInverse | kSse, r->all.d_items, r->all.d_tb, r->d_bank, r->all.nitems,
-                         r->all.ntiles, plan, s);
+                         r->all.ntiles, plan, s, r->d_counter);
         if (e != cudaSuccess) return cuda_fail(e, "verification pass");
         k_rc_frame_sse<<<blocks_for(nframes), 128, 0, s>>>(r->all.d_items, nframes, k, r->d_fsse);
         k_rc_decide<<<blocks_for(nframes), 128, 0, s>>>(r->d_fsse, r->d_blo, r->d_bhi, nframes, r->d_sse, r->d_fell);

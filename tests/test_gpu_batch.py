@@ -281,3 +281,36 @@ def test_batch_sse_restarts_between_batches(D):
         D.dct_batch_launch(plan)
         torch.cuda.synchronize()
         assert [int(v) for v in sse.cpu()] == [oracle(it)[2] for it in items_b]
+
+
+def test_batch_claimed_chunks_match_one_lane_ranges(D):
+    """A small grid over many tiles (at least 16 per warp) makes the two-lane
+    kernel claim four tiles at a time; its coefficients, reconstructions and
+    SSE equal the one-lane kernel's fixed-range results bit for bit, and
+    sampled blocks equal the oracle."""
+    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    srcs = [powerlaw_image(1600, 1600 - 8 * i, seed=40 + i, device="cuda") for i in range(4)]
+    quals = [30, 50, 75, 95]
+    out = {}
+    with D.Plan(1600, 1600, max_batch=4) as plan:
+        for lanes, shape in ((2, (64, 1, 32, 2)), (1, (256, 2, 32, 1))):
+            coefs = [torch.empty(D.coeff_count([s.shape]), dtype=torch.int16, device="cuda") for s in srcs]
+            recs = [torch.empty_like(s) for s in srcs]
+            sse = torch.zeros(4, dtype=torch.int64, device="cuda")
+            D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals, coeffs=coefs, recons=recs), C | R | S,
+                                sse=sse, shape=shape)
+            for _ in range(2):
+                D.dct_batch_launch(plan)
+            torch.cuda.synchronize()
+            out[lanes] = (coefs, recs, sse.clone())
+    ntiles = sum((((s.shape[0] + 7) // 8) * ((s.shape[1] + 7) // 8) + 31) // 32 for s in srcs)
+    assert ntiles >= 16 * torch.cuda.get_device_properties(0).multi_processor_count * 2   # warps of the small grid
+    for a, b in zip(out[2][0] + out[2][1], out[1][0] + out[1][1]):
+        assert torch.equal(a, b)
+    assert torch.equal(out[2][2], out[1][2])
+    it = dict(img=srcs[3][:64, :64].cpu().numpy(), quality=quals[3], chroma=False)
+    c_or, r_or, _ = oracle(it)
+    nbx = (srcs[3].shape[1] + 7) // 8
+    cb = out[2][0][3].view(-1, nbx, 8, 8)[:8, :8].cpu().numpy().reshape(-1)
+    assert np.array_equal(cb, c_or)
+    assert np.array_equal(out[2][1][3][:64, :64].cpu().numpy(), r_or)
