@@ -45,6 +45,11 @@ int main(void) {
     st[16 + 0x00] = 8;             /* eight EOBs: 0 bits */
     st[272] = 12;                  /* amplitude bits */
     CHECK(fabs(dct_entropy_bits(st) - 20.0) < 1e-12);
+    /* prefix codes: DC {4, 4} -> 1 bit each; the lone AC symbol -> 1 bit each */
+    CHECK(dct_huffman_bits(st) == 12 + 8 + 8);
+    st[0] = 1; st[1] = 1; st[2] = 2; st[3] = 4;   /* DC lengths 3, 3, 2, 1: 14 bits */
+    CHECK(dct_huffman_bits(st) == 12 + 14 + 8);
+    CHECK(dct_huffman_bits(NULL) == 0);
 
     dct_plan_t plan = NULL;
     dct_plan_desc desc = {0, 10, DCT_LAYOUT_GRAY8, 0, 0};
