@@ -120,12 +120,22 @@ def algorithmic_ops_per_sample():
 KERNEL_SOURCES = ("batch.cu", "kernels.cuh", "kernels_pair.cuh", "cordic_loeffler.cuh", "dctgb_spec.h")
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace runs collapsed, so a
+    comment edit does not count as a kernel change."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_sha():
-    """Hash of the files that define the batched kernels (the dominant kernel)."""
+    """Hash of the code (comments aside) of the files that define the batched
+    kernels (the dominant kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1306_1373_gb300", "csrc")
     for fn in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, fn), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, fn)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,4 +1,5 @@
-// Fused codec tile with two lanes per 8x8 block.
+// Codec tile with two lanes per 8x8 block: the fused pass, the forward pass
+// alone and the inverse pass alone.
 //
 // The one-lane-per-block tile (kernels.cuh) keeps all 64 samples of a block
 // in one thread, which makes the row/column transpose free but needs about
