@@ -4,10 +4,10 @@
 //
 // Work list: item i covers warp tiles [tile_begin[i], tile_begin[i+1]).
 // One-lane kernels: each warp takes one contiguous range of tiles (ranges
-// differ by at most one tile).  Two-lane kernels in the captured graph: each
-// warp claims its next tile from a counter the graph's first launch resets,
-// so warps that finish early keep working and the claimed tiles of a warp
-// only increase.  Either way consecutive tiles of a warp usually belong to
+// differ by at most one tile).  Two-lane kernels given a tile counter (the
+// captured graph, whose clearing launch resets it, and the rate controller's
+// passes): each warp claims its next tiles from the counter, so warps that
+// finish early keep working, and the claimed tiles of a warp only increase.  Either way consecutive tiles of a warp usually belong to
 // the same item: the warp keeps that item's descriptor and tables in its own
 // shared memory slot and accumulates the item's SSE in a register, flushing
 // it with one atomic add when the item changes.
@@ -27,9 +27,9 @@ struct BatchArgs {
     const QuantSet* tabs;       // unique tables
     int32_t nitems;
     int32_t ntiles;
-    // Two-lane kernels: when set, warps claim tiles one at a time from this
-    // counter (zero on entry, reset by k_batch_init) instead of taking a
-    // fixed contiguous range; warps that finish early keep working.
+    // Two-lane kernels: when set, warps claim tiles from this counter (zero on
+    // entry: k_batch_init or the caller resets it) instead of taking a fixed
+    // contiguous range; warps that finish early keep working.
     unsigned int* next_tile;
 };
 
