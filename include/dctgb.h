@@ -272,7 +272,11 @@ typedef struct {
 dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n, uint32_t ops,
                              uint64_t* sse_out, const dct_launch_shape* shape, dct_stream_t stream);
 
-/* Replays the prepared graph on `stream`.  DCT_ERR_STATE if nothing is prepared. */
+/* Replays the prepared graph on `stream`.  DCT_ERR_STATE if nothing is
+ * prepared.  Replays of one plan must not overlap on the GPU: they share the
+ * plan's tile counters (the two-lane kernels claim their tiles from them) and
+ * their first launch re-clears the SSE words; streams that run batches
+ * concurrently each need a plan of their own. */
 dct_status dct_batch_launch(dct_plan_t plan, dct_stream_t stream);
 
 /* Times candidate launch shapes for the prepared batch (CUDA events on
