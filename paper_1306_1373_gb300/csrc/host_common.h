@@ -40,8 +40,8 @@ struct dct_plan_s {
 namespace dctgb {
 
 // Launch shape of the batched kernels until dct_autotune picks one: 256
-// threads, 8 CTAs per SM (oversubscribed: shorter contiguous tile ranges),
-// two lanes per block for the fused operations.
+// threads, a grid of 8 CTAs per SM (more than fit at once), two lanes per
+// block for the operations that have a two-lane form.
 inline dct_launch_shape default_shape() { return dct_launch_shape{256, 8, kTileBlocks, 2}; }
 
 // Checks one plane against the plan limits; `what` names it in errors.
