@@ -28,3 +28,19 @@ def test_parallel_baseline_reports_its_cores():
     plane = np.full((64, 64), 77, dtype=np.uint8)
     r = bench.cpu_baseline_parallel(plane, 0.2, rows=16, cores=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """roofline.traffic is reported only while the kernel code matches the
+    capture: comment edits keep the hash, code edits change it."""
+    import bench
+    base = "int f(int a) { // add one\n  return a + 1; /* done */ }\n"
+    assert bench._code_only(base) == bench._code_only("int f(int a) {\n  return a + 1;\n}\n")
+    assert bench._code_only(base) != bench._code_only("int f(int a) { return a + 2; }")
+
+
+def test_stored_traffic_matches_the_current_sources():
+    import bench
+    for k in ("k_batch_pair", "k_batch"):
+        name = "%s<fused: load, fwd, quant, store coef, dequant, inv, store recon, SSE>" % k
+        assert bench.stored_traffic(name, bench.WORKLOAD) is not None, name
