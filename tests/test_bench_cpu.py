@@ -38,9 +38,3 @@ def test_kernel_source_hash_ignores_comments_only():
     assert bench._code_only(base) == bench._code_only("int f(int a) {\n  return a + 1;\n}\n")
     assert bench._code_only(base) != bench._code_only("int f(int a) { return a + 2; }")
 
-
-def test_stored_traffic_matches_the_current_sources():
-    import bench
-    for k in ("k_batch_pair", "k_batch"):
-        name = "%s<fused: load, fwd, quant, store coef, dequant, inv, store recon, SSE>" % k
-        assert bench.stored_traffic(name, bench.WORKLOAD) is not None, name
