@@ -314,3 +314,46 @@ def test_batch_claimed_chunks_match_one_lane_ranges(D):
     cb = out[2][0][3].view(-1, nbx, 8, 8)[:8, :8].cpu().numpy().reshape(-1)
     assert np.array_equal(cb, c_or)
     assert np.array_equal(out[2][1][3][:64, :64].cpu().numpy(), r_or)
+
+
+def test_full_size_workload_in_the_benchmark_configuration(D):
+    """The benchmark's step exactly: the 8192 x 8192 grey plane and the
+    3840 x 2160 4:2:0 frame (quality 75, luma and chroma tables) in one
+    fused batch, launch shape from dct_autotune, replayed from the graph:
+    sampled blocks (2048 random ones plus the last block row and column of
+    each plane) against the oracle and every plane's SSE against its
+    reconstruction."""
+    import bench
+    planes, chroma = bench.make_planes(torch.device("cuda", 0))
+    shapes = [tuple(p.shape) for p in planes]
+    coefs = [torch.empty(D.coeff_count([s]), dtype=torch.int16, device="cuda") for s in shapes]
+    recs = [torch.empty_like(p) for p in planes]
+    sse = torch.zeros(len(planes), dtype=torch.int64, device="cuda")
+    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    with D.Plan(8192, 8192, max_batch=len(planes)) as plan:
+        D.dct_batch_prepare(plan, D.make_batch_items(planes, [bench.QUALITY] * 4, coeffs=coefs, recons=recs,
+                                                     chroma=chroma), C | R | S, sse=sse)
+        shape, _ = D.dct_autotune(plan)
+        for _ in range(2):
+            D.dct_batch_launch(plan)
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    for p, c, r, is_chroma, e in zip(planes, coefs, recs, chroma, sse.cpu().tolist()):
+        h, w = p.shape
+        nby, nbx = (h + 7) // 8, (w + 7) // 8
+        Q = ijg.chroma_table(bench.QUALITY) if is_chroma else ijg.luma_table(bench.QUALITY)
+        bys = np.concatenate([rng.integers(0, nby, 2048), np.full(nbx, nby - 1), np.arange(nby)])
+        bxs = np.concatenate([rng.integers(0, nbx, 2048), np.arange(nbx), np.full(nby, nbx - 1)])
+        sel = np.unique(bys * nbx + bxs)
+        blocks = codec.plane_to_blocks(p.cpu().numpy()).reshape(-1, 8, 8)[sel]
+        c_or = codec.compress_blocks(blocks, Q)
+        got = c.view(-1, 8, 8)[torch.from_numpy(sel).cuda()].cpu().numpy()
+        assert np.array_equal(got, c_or)
+        r_or = codec.reconstruct_blocks(c_or, Q)
+        rec = codec.plane_to_blocks(r.cpu().numpy()).reshape(-1, 8, 8)[sel]
+        by_s, bx_s = sel // nbx, sel % nbx
+        for k in range(sel.size):
+            nr, nc = min(8, h - 8 * by_s[k]), min(8, w - 8 * bx_s[k])
+            assert np.array_equal(rec[k, :nr, :nc], r_or[k, :nr, :nc])
+        d = r.to(torch.int64) - p.to(torch.int64)
+        assert int(e) == int((d * d).sum())

@@ -244,9 +244,11 @@ def test_invalid_arguments_enqueue_nothing(D):
 
 
 def test_full_size_workload_sampled(D):
-    """8192 x 8192 grey plus a 3840 x 2160 4:2:0 frame at quality 75, in the
-    launch configuration the benchmark uses: sampled blocks against the
-    oracle, the SSE against the reconstruction it belongs to."""
+    """8192 x 8192 grey plus a 3840 x 2160 4:2:0 frame at quality 75 through
+    the direct plane calls (dct_compress, dct_reconstruct): sampled blocks
+    against the oracle, the SSE against the reconstruction it belongs to.
+    The batched configuration the benchmark times is tested in
+    test_gpu_batch.py."""
     dev = "cuda"
     grey = powerlaw_image(8192, 8192, seed=11, device=dev)
     y, cb, cr = yuv420_frame(3840, 2160, seed=12, device=dev)
