@@ -124,7 +124,7 @@ dct_status dct_plan_destroy(dct_plan_t plan);
  *                   16-byte aligned.
  *  stats_out        optional (NULL = skip) device uint64 array of
  *                   dct_spec_info.stats_words words per plane, overwritten:
- *                   words 0..63 band energies sum_blocks ((|Y_uv| >> P)^2),
+ *                   words 0..63 band energies sum_blocks ((|Y_uv| >> (P+1))^2),
  *                   then pixel statistics (see dct_stats_layout in the
  *                   Python binding): sum p, sum p^2, min p, max p,
  *                   sum |dx|, sum |dy|, sum dx^2, sum dy^2 (within blocks),
