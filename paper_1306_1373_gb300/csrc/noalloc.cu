@@ -15,6 +15,12 @@
 // the process.  In host code its name is only a host-side stand-in, so the
 // device address is looked up with cudaGetSymbolAddress once per device, on
 // that device's first call, and kept in a per-device table.
+//
+// The descriptors and tables are staged in this call's stack frame and
+// copied with cudaMemcpyAsync from that pageable memory: the driver may
+// first wait for the work already queued on the stream, and the call refuses
+// to run while the stream is being captured (a graph would replay copies
+// from a frame that no longer exists).
 #include <cstring>
 
 #include "host_common.h"
@@ -61,65 +67,61 @@ extern "C" dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, 
     const bool two = ops & DCT_OP_TWO_PASS;
     if (two && !(comp && rec)) return fail(DCT_ERR_INVALID_ARG, "DCT_OP_TWO_PASS needs COMPRESS|RECONSTRUCT");
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(DCT_ERR_UNSUPPORTED, "device index beyond 63");
-    if (!g_list_addr[dev]) {
-        // first call on this device: find where the array lives on it
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_list);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        g_list_addr[dev] = static_cast<NoAllocList*>(p);
-    }
-    NoAllocList* dlist = g_list_addr[dev];
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-
-    // A plan on the stack carries the limits and launch shape the shared
-    // launcher reads; nothing is allocated.
-    dct_plan_s plan;
-    memset(&plan, 0, sizeof plan);
-    plan.desc.max_width = 1 << 16;
-    plan.desc.max_height = 1 << 16;
-    plan.desc.layout = DCT_LAYOUT_GRAY8;
-    plan.desc.max_batch = kNoAllocMaxItems;
-    plan.device = dev;
-    plan.num_sms = sms;
-    plan.shape = dct_launch_shape{256, 0, kTileBlocks, 0};
-
     unsigned mode;
     if (two) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
     else if (comp && !rec && !sse) mode = kLoadPix | kStoreCoef;
     else if (rec && !comp) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
     else mode = kLoadPix | kInverse | (sse ? kSse : 0u) | (comp ? kStoreCoef : 0u) | (rec ? kStoreRecon : 0u);
 
-    // descriptors staged on the stack (pageable: cudaMemcpyAsync has copied
-    // them out when it returns); tables go up one at a time as they appear
+    // A plan on the stack carries the limits and launch shape the shared
+    // launcher reads; nothing is allocated.  The shape is a new plan's
+    // default (two lanes per block where the operation has a two-lane
+    // kernel); without a tile counter those kernels give each warp a fixed
+    // contiguous tile range, so no device word is needed.
+    dct_plan_s plan;
+    memset(&plan, 0, sizeof plan);
+    plan.desc.max_width = 1 << 16;
+    plan.desc.max_height = 1 << 16;
+    plan.desc.layout = DCT_LAYOUT_GRAY8;
+    plan.desc.max_batch = kNoAllocMaxItems;
+    plan.shape = default_shape();
+
+    // Pass 1, host only: check every item against the limits of
+    // dct_plan_create (at most 65536 x 65536, below 2^31 samples per plane)
+    // and dct_batch_prepare (source samples are needed only when the
+    // operation reads them; at most 2^30 tiles), fill the descriptors in a
+    // stack buffer and assign table slots.  Nothing touches the GPU until
+    // every item is valid.
     struct {
         PlaneArg items[kNoAllocMaxItems];
         int32_t tile_begin[kNoAllocMaxItems + 1];
     } h;
     QuantSet tab;
-    cudaStream_t s = (cudaStream_t)stream;
     int cursor = 0, ntabs = 0;
     int tab_quality[kNoAllocMaxItems], tab_chroma[kNoAllocMaxItems], tab_item[kNoAllocMaxItems];
     const uint16_t* tab_custom[kNoAllocMaxItems];
-    // pass 1: check every item and assign table slots; nothing is enqueued
-    // until all of them are valid
+    const bool need_src = (mode & kLoadPix) || (mode & kSse) || two;
     for (int i = 0; i < n; ++i) {
         const dct_batch_item& it = items[i];
-        dct_status st = check_plane(&plan, it.src, "item src");
-        if (st != DCT_OK) return st;
+        dct_status st = DCT_OK;
+        if (need_src) {
+            if ((st = check_plane(&plan, it.src, "item src")) != DCT_OK) return st;
+        } else if (it.src.width < 1 || it.src.height < 1 || it.src.width > plan.desc.max_width ||
+                   it.src.height > plan.desc.max_height) {
+            return fail(DCT_ERR_INVALID_ARG, "item size outside 1..65536 x 1..65536");
+        }
+        if ((int64_t)it.src.width * it.src.height > (int64_t)1 << 31)
+            return fail(DCT_ERR_INVALID_ARG, "item width * height must stay below 2^31 samples");
         PlaneArg& a = h.items[i];
         memset(&a, 0, sizeof a);
         fill_plane(a, it.src, cursor);
+        if (cursor < 0 || cursor > (1 << 30)) return fail(DCT_ERR_INVALID_ARG, "batch too large");
         a.src = it.src.data;
         a.src_pitch = it.src.pitch;
         a.ref = it.src.data;
         a.ref_pitch = it.src.pitch;
-        int fl = ((((uintptr_t)it.src.data) & 7u) == 0 && (it.src.pitch & 7) == 0) ? (kVecSrc | kVecRef) : 0;
+        int fl = (it.src.data && (((uintptr_t)it.src.data) & 7u) == 0 && (it.src.pitch & 7) == 0) ? (kVecSrc | kVecRef)
+                                                                                                  : 0;
         if ((mode & kStoreCoef) || (mode & kLoadCoef)) {
             if (!it.coeffs) return fail(DCT_ERR_INVALID_ARG, "item coeffs is null");
             if (((uintptr_t)it.coeffs) & 15u) return fail(DCT_ERR_INVALID_ARG, "item coeffs must be 16-byte aligned");
@@ -153,15 +155,44 @@ extern "C" dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, 
         a.table = t;
         h.tile_begin[i] = a.tile_begin;
     }
-    // pass 2: upload the distinct tables from one stack buffer each
+    h.tile_begin[n] = cursor;
+
+    // The descriptors are copied from this call's stack frame.  Captured into
+    // a graph, those copies would read a frame that is gone when the graph
+    // replays, so the call refuses to run on a stream that is capturing.
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(DCT_ERR_UNSUPPORTED, "dct_batch_run_noalloc does not run on a stream that is being captured "
+                                         "(its descriptors are copied from the caller's stack)");
+
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(DCT_ERR_UNSUPPORTED, "device index beyond 63");
+    if (!g_list_addr[dev]) {
+        // first call on this device: find where the array lives on it
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_list);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_list_addr[dev] = static_cast<NoAllocList*>(p);
+    }
+    NoAllocList* dlist = g_list_addr[dev];
+    e = cudaDeviceGetAttribute(&plan.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    plan.device = dev;
+
+    // Pass 2: upload the distinct tables from one stack buffer each, then
+    // the descriptors (pageable copies: cudaMemcpyAsync has read them when
+    // it returns).
     for (int k = 0; k < ntabs; ++k) {
         const dct_batch_item& it = items[tab_item[k]];
         build_tables(it.quality, it.qtab_host, 64, it.chroma, tab);
         e = cudaMemcpyAsync(dlist->tabs + k, &tab, sizeof(QuantSet), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "table upload");
     }
-    h.tile_begin[n] = cursor;
-
     e = cudaMemcpyAsync(dlist->items, h.items, sizeof(PlaneArg) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dlist->tile_begin, h.tile_begin, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
