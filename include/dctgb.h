@@ -178,6 +178,24 @@ dct_status dct_exact_fused(dct_plan_t plan, const dct_plane* planes, int nplanes
 dct_status dct_rgb_to_yuv420(const uint8_t* rgb, int32_t width, int32_t height, int32_t rgb_pitch,
                              const dct_plane* y, const dct_plane* cb, const dct_plane* cr, dct_stream_t stream);
 
+/* RGB input straight into the forward path (no counterpart in the paper,
+ * which codes grey images): the RGB -> YCbCr 4:2:0 conversion of
+ * dct_rgb_to_yuv420 fused with dct_compress of the three planes, so the
+ * planes never reach device memory (3 bytes per pixel in, the codes out).
+ * The codes equal those of dct_rgb_to_yuv420 followed by dct_compress on the
+ * planes [Y (width x height), Cb, Cr (ceil(width/2) x ceil(height/2))] with
+ * the luminance table for Y and the chrominance table for Cb and Cr.
+ *  rgb            device, interleaved R,G,B bytes; row r starts at
+ *                 rgb + r * rgb_pitch (rgb_pitch >= 3 * width)
+ *  width, height  within the plan's limits
+ *  quality/qtab   as dct_compress under DCT_LAYOUT_YUV420 (64 entries: one
+ *                 table for all three planes; 128: luma, then chroma)
+ *  coeffs         device int16, 16-byte aligned: Y codes, then Cb, then Cr,
+ *                 laid out as dct_compress writes them for those planes. */
+dct_status dct_compress_rgb(dct_plan_t plan, const uint8_t* rgb, int32_t width, int32_t height, int32_t rgb_pitch,
+                            int quality, const uint16_t* qtab_host, int qtab_entries, int16_t* coeffs,
+                            dct_stream_t stream);
+
 /* Rate of quantised coefficients (no counterpart in the paper, which never
  * measures the compressed size): counts of the JPEG-style symbols of each
  * plane.  Per plane DCT_ENTROPY_WORDS uint64 words (device, overwritten):
@@ -215,6 +233,14 @@ dct_status dct_psnr(dct_plan_t plan, const dct_plane* a, const dct_plane* b, int
 /* Host only: PSNR = 10 log10(max_value^2 * n / sse) (Eq. 23 with Eq. 24);
  * +inf for sse == 0; max_value 0 means 255. */
 double dct_psnr_from_sse(uint64_t sse, int64_t n_samples, double max_value);
+
+/* Host only: PSNR (Eq. 23 with Eq. 24) of n planes from their SSEs and
+ * sample counts, and the sample-weighted PSNR over all of them (one MSE
+ * over the union of their samples, the combined figure of a 4:2:0 frame).
+ * psnr_host receives n + 1 values; +inf where an SSE is 0; max_value 0
+ * means 255.  Sample counts must be >= 1. */
+dct_status dct_psnr_from_sse_list(const uint64_t* sse_host, const int64_t* samples_host, int n, double max_value,
+                                  double* psnr_host);
 
 /* ---------------------------------------------------------------------
  * Batched path: many images of uneven sizes and qualities in one
@@ -336,6 +362,11 @@ dct_status dct_mlp_set_norm(dct_mlp* net, const float* feats, int n, dct_stream_
 dct_status dct_mlp_forward(const dct_mlp* net, const float* feats, int n, float* y_out, int32_t* quality_out,
                            dct_stream_t stream);
 
+/* Training targets of n quality labels (device int32, 1..100): labels_out
+ * (device float[n]) = (Q - 1) / 99, the value the network's output y
+ * predicts. */
+dct_status dct_mlp_labels(const int32_t* quality, int n, float* labels_out, dct_stream_t stream);
+
 /* Bytes of device workspace dct_mlp_loss_grad needs for a minibatch of `batch` rows. */
 size_t dct_mlp_workspace_bytes(int batch);
 
@@ -362,7 +393,10 @@ dct_status dct_mlp_train_epoch(dct_mlp* net, const float* feats, const float* la
 typedef struct {
     int32_t frames;        /* frames processed */
     int32_t fell_back;     /* frames that went through the bisection */
-    int32_t unreachable;   /* frames whose PSNR at quality 100 is below the target */
+    int32_t unreachable;   /* frames whose final PSNR is outside the 0.25 dB band: the
+                            * bisection evaluated the qualities on both sides of the
+                            * band (or ended at 1 or 100), so no quality lands in it
+                            * while PSNR rises with quality */
     int32_t within_tol;    /* frames whose final PSNR is within 0.25 dB of the target */
     int32_t passes;        /* full-pipeline passes over frames (sum over frames) */
     float gpu_ms;          /* device time of the call (CUDA events on `stream`) */
@@ -373,7 +407,9 @@ typedef struct {
  * chrominance table for planes 1 and 2).  A frame's PSNR is Eq. 23 over all
  * of its samples with MAX 255.  With net == NULL every frame is bisected
  * (8 passes: lo = 1, hi = 100, mid = (lo + hi) / 2, hi = mid if
- * PSNR(mid) >= target else lo = mid + 1; the result is hi).  With a network,
+ * PSNR(mid) >= target else lo = mid + 1, giving Q* = hi; when PSNR(Q*) is
+ * more than 0.25 dB from the target but the last rejected quality, Q* - 1,
+ * is within 0.25 dB, the result is Q* - 1).  With a network,
  * the statistics pass, features and network give a quality, one pass
  * verifies it, and frames whose PSNR misses the target by more than 0.25 dB
  * (either way) fall back to the bisection.  Decisions compare the integer
@@ -403,17 +439,50 @@ dct_status dct_rate_features(dct_plan_t plan, const dct_plane* planes, int plane
  *  - The work list goes to a fixed array inside the library image
  *    (about 70 KB on every device that loads the library, held until the
  *    process exits).  n is limited to 1..64 items; larger n returns
- *    DCT_ERR_INVALID_ARG.
+ *    DCT_ERR_INVALID_ARG.  Each item obeys the limits of a plan: at most
+ *    65536 x 65536 and below 2^31 samples.
  *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress).
  *  - Every call on a device shares the array and overwrites it.  Calls that
  *    overlap on the GPU (different streams, or host threads racing) race on
  *    it: serialise them.  sse_out is cleared by the call itself.
  *  - The descriptors are copied from the caller's stack with
- *    cudaMemcpyAsync on `stream` (pageable: the call returns once they are
- *    staged). */
+ *    cudaMemcpyAsync on `stream`.  That memory is pageable, so the driver
+ *    may first wait for the work already queued on `stream`; the call
+ *    returns once the descriptors are staged.  For the same reason the call
+ *    returns DCT_ERR_UNSUPPORTED, enqueuing nothing, while `stream` is being
+ *    captured into a graph.
+ *  - Launch shape: a new plan's default (two lanes per block where the
+ *    operation has a two-lane kernel, fixed tile ranges per warp). */
 dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, uint32_t ops, uint64_t* sse_out,
                                  dct_stream_t stream);
+
+/* Integer issue-rate probe (no counterpart in the paper; measurement helper
+ * for the roofline of the codec kernels, which are bound by integer
+ * instruction issue).  Runs `iters` iterations of 32 CORDIC micro-rotations
+ * (a, b) <- (a + (b >> i), b - (a >> i)), i in 2..6, per thread on 8
+ * independent chains, over every SM, in one of three instruction forms:
+ * kind 0 shift + add for both halves (the form the codec kernels use);
+ * kind 1 one half as mad.hi.s32, the other as shift + add; kind 2 both
+ * halves as mad.hi.s32.  Counts 4 integer operations (2 floor shifts, 2 adds) per
+ * micro-rotation.  Host outputs (any may be NULL): operations per clock per
+ * SM (from clock64 spans, independent of the clock the GPU ran at),
+ * Tops/s and the kernel time in ms.  Allocates two small device buffers;
+ * synchronises `stream`.  iters in 1..2^24. */
+dct_status dct_int_peak(int kind, int iters, double* ops_per_clk_sm_host, double* tops_host, float* ms_host,
+                        dct_stream_t stream);
+
+/* Test hook for the failure paths (no counterpart in the paper): arms the
+ * library so that the nth allocation attempt from now (device or pinned
+ * memory, stream or event creation of a plan's workspaces: the batch work
+ * list, the rate-control state, the autotuner's events and flush buffer)
+ * fails as if the device were out of memory, without calling CUDA; the
+ * call that meets it returns DCT_ERR_ALLOC having enqueued nothing, and
+ * the hook disarms (the autotuner's flush buffer is optional: without it
+ * the candidates are timed warm).  nth = 0 disarms it.  attempts_host (may be NULL)
+ * receives the number of attempts counted since the library loaded.  Host
+ * only; never touches the GPU. */
+dct_status dct_debug_fail_alloc(int nth, int64_t* attempts_host);
 
 /* Thread-local description of the last error on this thread. */
 const char* dct_last_error(void);

@@ -121,23 +121,24 @@ def descale(v, r=None):
     return np.clip(out, 0, 255).astype(np.uint8)
 
 
-def compress_blocks(blocks_u8, qtab, sig=None):
-    """(n, 8, 8) uint8 blocks -> (n, 8, 8) int16 quantised coefficients."""
-    y = forward_2d(level_shift(blocks_u8), sig)
-    q = quantize(y, quant_multipliers(qtab))
+def compress_blocks(blocks_u8, qtab, n=None):
+    """(n, 8, 8) uint8 blocks -> (n, 8, 8) int16 quantised coefficients, with
+    N = n CORDIC micro-rotations per rotation (None: the spec's)."""
+    y = forward_2d(level_shift(blocks_u8), Sigmas(n))
+    q = quantize(y, quant_multipliers(qtab, n))
     assert np.abs(q).max(initial=0) < (1 << 15)
     return q.astype(np.int16)
 
 
-def reconstruct_blocks(coeffs, qtab, sig=None):
+def reconstruct_blocks(coeffs, qtab, n=None):
     """(n, 8, 8) int16 coefficients -> (n, 8, 8) uint8 reconstructed blocks."""
-    g = dequantize(coeffs, qtab, dequant_weights())
-    return descale(inverse_2d(g, sig))
+    g = dequantize(coeffs, qtab, dequant_weights(n))
+    return descale(inverse_2d(g, Sigmas(n)))
 
 
-def forward_coefficients(blocks_u8, sig=None):
+def forward_coefficients(blocks_u8, n=None):
     """The unquantised forward output Y (int64), for statistics."""
-    return forward_2d(level_shift(blocks_u8), sig)
+    return forward_2d(level_shift(blocks_u8), Sigmas(n))
 
 
 # --------------------------------------------------------------------------
@@ -171,11 +172,11 @@ def blocks_to_plane(blocks, height, width):
     return full[:height, :width]
 
 
-def compress_plane(img, qtab):
+def compress_plane(img, qtab, n=None):
     """uint8 (H, W) plane -> int16 coefficients (nby, nbx, 8, 8), block-major."""
-    return compress_blocks(plane_to_blocks(img), qtab)
+    return compress_blocks(plane_to_blocks(img), qtab, n)
 
 
-def reconstruct_plane(coeffs, qtab, height, width):
+def reconstruct_plane(coeffs, qtab, height, width, n=None):
     """int16 (nby, nbx, 8, 8) coefficients -> uint8 (H, W) reconstruction."""
-    return blocks_to_plane(reconstruct_blocks(coeffs, qtab), height, width)
+    return blocks_to_plane(reconstruct_blocks(coeffs, qtab, n), height, width)

@@ -70,14 +70,15 @@ def forward_bounds(p=None, sig=None):
     return tr1.max_abs, tr2.max_abs, out
 
 
-def inverse_bounds(dc_offset=0, sig=None):
+def inverse_bounds(dc_offset=0, sig=None, n=None):
     """Run the inverse 2-D transform on the intervals the dequantiser can
     produce (|clamp(qQ)| <= 4096 times W_uv).  ``dc_offset`` adds a constant
     to the (0, 0) input, covering implementations that fold the descale
-    rounding term into the DC coefficient.  Returns (max |node| in the
-    column pass, max |node| in the row pass)."""
-    sig = Sigmas() if sig is None else sig
-    w = dequant_weights()
+    rounding term into the DC coefficient.  n: CORDIC micro-rotations per
+    rotation (None: the spec's).  Returns (max |node| in the column pass,
+    max |node| in the row pass)."""
+    sig = Sigmas(n) if sig is None else sig
+    w = dequant_weights(n)
     tr1 = Tracker()
     cols = []
     for v in range(8):
@@ -94,8 +95,8 @@ def inverse_bounds(dc_offset=0, sig=None):
     return tr1.max_abs, tr2.max_abs
 
 
-def worst_case_product_bits(y_bound, qtab_min=1):
+def worst_case_product_bits(y_bound, qtab_min=1, n=None):
     """Bits needed by |Y| * M + 2^31 in the quantiser for the largest M."""
     from .codec import quant_multipliers
-    m = int(np.max(quant_multipliers(np.full((8, 8), qtab_min))))
+    m = int(np.max(quant_multipliers(np.full((8, 8), qtab_min), n)))
     return (y_bound * m + (1 << 31)).bit_length(), m

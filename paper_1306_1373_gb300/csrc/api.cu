@@ -1,6 +1,7 @@
 // C ABI of the codec: spec query, tables, plans, compress / reconstruct /
 // fused / PSNR entry points.  Every argument is checked here before anything
 // is enqueued; the kernels themselves never trap.
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <cstdio>
@@ -23,7 +24,41 @@ dct_status fail(dct_status st, const std::string& msg) {
 dct_status cuda_fail(cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     set_error(m);
-    return DCT_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? DCT_ERR_ALLOC : DCT_ERR_CUDA;
+}
+
+// Fault injection of the workspace allocations: 0 = off; n > 0 = the n-th
+// attempt from now fails (and disarms the hook).
+static std::atomic<int> g_fail_at{0};
+static std::atomic<long long> g_alloc_attempts{0};
+
+static bool injected_failure() {
+    g_alloc_attempts.fetch_add(1);
+    int n = g_fail_at.load();
+    while (n > 0) {
+        if (g_fail_at.compare_exchange_weak(n, n - 1)) return n == 1;
+    }
+    return false;
+}
+
+cudaError_t ws_malloc(void** p, size_t bytes) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t ws_malloc_host(void** p, size_t bytes) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(p, bytes);
+}
+
+cudaError_t ws_stream_create(cudaStream_t* s) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+
+cudaError_t ws_event_create(cudaEvent_t* e) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaEventCreate(e);
 }
 
 // ITU-T T.81 Annex K, Table K.1 (luminance) and Table K.2 (chrominance),
@@ -137,6 +172,13 @@ extern "C" {
 
 const char* dct_last_error(void) { return g_last_error.c_str(); }
 
+dct_status dct_debug_fail_alloc(int nth, int64_t* attempts_host) {
+    if (nth < 0) return fail(DCT_ERR_INVALID_ARG, "nth must be >= 0");
+    g_fail_at.store(nth);
+    if (attempts_host) *attempts_host = g_alloc_attempts.load();
+    return DCT_OK;
+}
+
 dct_status dct_spec_query(dct_spec_info* out) {
     if (!out) return fail(DCT_ERR_INVALID_ARG, "out is null");
     out->P = kP;
@@ -169,6 +211,22 @@ double dct_psnr_from_sse(uint64_t sse, int64_t n_samples, double max_value) {
     const double mx = max_value > 0.0 ? max_value : (double)kPsnrMax;
     if (sse == 0) return INFINITY;
     return 10.0 * std::log10(mx * mx * (double)n_samples / (double)sse);
+}
+
+dct_status dct_psnr_from_sse_list(const uint64_t* sse_host, const int64_t* samples_host, int n, double max_value,
+                                  double* psnr_host) {
+    if (!sse_host || !samples_host || !psnr_host) return fail(DCT_ERR_INVALID_ARG, "null pointer");
+    if (n < 1) return fail(DCT_ERR_INVALID_ARG, "n must be >= 1");
+    uint64_t tot = 0;
+    int64_t ns = 0;
+    for (int i = 0; i < n; ++i) {
+        if (samples_host[i] < 1) return fail(DCT_ERR_INVALID_ARG, "sample counts must be >= 1");
+        psnr_host[i] = dct_psnr_from_sse(sse_host[i], samples_host[i], max_value);
+        tot += sse_host[i];
+        ns += samples_host[i];
+    }
+    psnr_host[n] = dct_psnr_from_sse(tot, ns, max_value);
+    return DCT_OK;
 }
 
 dct_status dct_plan_create(dct_plan_t* out, const dct_plan_desc* desc, dct_stream_t stream) {

@@ -329,14 +329,14 @@ static dct_status ensure_state(dct_plan_t plan) {
     if (!b) return fail(DCT_ERR_ALLOC, "host allocation failed");
     b->cap = cap;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(PlaneArg) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_begin, sizeof(int32_t) * (cap + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tabs, sizeof(QuantSet) * cap);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(PlaneArg) * cap);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tile_begin, sizeof(int32_t) * (cap + 1));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tabs, sizeof(QuantSet) * cap);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = ws_malloc((void**)&b->d_items, sizeof(PlaneArg) * cap);
+    if (e == cudaSuccess) e = ws_malloc((void**)&b->d_tile_begin, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = ws_malloc((void**)&b->d_tabs, sizeof(QuantSet) * cap);
+    if (e == cudaSuccess) e = ws_malloc((void**)&b->d_counters, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = ws_malloc_host((void**)&b->h_items, sizeof(PlaneArg) * cap);
+    if (e == cudaSuccess) e = ws_malloc_host((void**)&b->h_tile_begin, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = ws_malloc_host((void**)&b->h_tabs, sizeof(QuantSet) * cap);
+    if (e == cudaSuccess) e = ws_stream_create(&b->cap_stream);
     if (e != cudaSuccess) {
         release(b);
         return fail(DCT_ERR_ALLOC, std::string("batch workspace: ") + cudaGetErrorString(e));
@@ -582,9 +582,9 @@ dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host,
     if (!plan->batch || !plan->batch->prepared) return fail(DCT_ERR_STATE, "no prepared batch");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
-    cudaError_t e = cudaEventCreate(&e0);
+    cudaError_t e = ws_event_create(&e0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if ((e = ws_event_create(&e1)) != cudaSuccess) {
         cudaEventDestroy(e0);
         return cuda_fail(e, "cudaEventCreate");
     }
@@ -594,7 +594,7 @@ dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host,
     void* flush = nullptr;
     size_t flush_bytes = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
-        l2 > 0 && cudaMalloc(&flush, 2 * (size_t)l2) == cudaSuccess)
+        l2 > 0 && ws_malloc(&flush, 2 * (size_t)l2) == cudaSuccess)
         flush_bytes = 2 * (size_t)l2;
     else
         cudaGetLastError();

@@ -7,8 +7,16 @@
 
 namespace dctgb {
 
+// CORDIC micro-rotations per rotation.  The spec file's value (6) is the
+// default; the build can compile the same library at another count
+// (-DDCTGB_CORDIC_N=4 or 5) to trade accuracy for integer operations.
+#ifndef DCTGB_CORDIC_N
+#define DCTGB_CORDIC_N 6
+#endif
+
 constexpr int kP = 4;              // x = (p - 128) << kP
-constexpr int kN = 6;              // CORDIC micro-rotations, shifts 1..kN
+constexpr int kN = DCTGB_CORDIC_N; // CORDIC micro-rotations, shifts 1..kN
+static_assert(kN >= 3 && kN <= 12, "CORDIC iteration count outside the supported range");
 constexpr int kR = 11;             // dequantiser weights carry 2^kR
 constexpr int kQuantShift = 32;    // quantiser multipliers carry 2^32
 constexpr int kDequantClamp = 4096;

@@ -17,6 +17,15 @@ void set_error(const std::string& msg);
 dct_status fail(dct_status st, const std::string& msg);
 dct_status cuda_fail(cudaError_t e, const char* what);
 
+// Allocations of the plan workspaces (batch work lists, rate-control state,
+// autotuner events and flush buffer) go through these, which count every
+// attempt and fail the one that dct_debug_fail_alloc armed with
+// cudaErrorMemoryAllocation, without calling CUDA.
+cudaError_t ws_malloc(void** p, size_t bytes);
+cudaError_t ws_malloc_host(void** p, size_t bytes);
+cudaError_t ws_stream_create(cudaStream_t* s);
+cudaError_t ws_event_create(cudaEvent_t* e);
+
 // Builds Q, M, W for one plane.  quality 1..100 scales the T.81 Annex K
 // table (chroma selects K.2); quality 0 takes qtab (64 or 128 entries).
 dct_status build_tables(int quality, const uint16_t* qtab, int qtab_entries, int chroma, QuantSet& out);

@@ -163,6 +163,13 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __re
 
 // mean and standard deviation of every feature (one thread per feature, in
 // row order, float64); a standard deviation below 1e-6 becomes 1
+// training target of a quality label: (Q - 1) / 99 (IEEE division, as the
+// host would compute it in float32)
+__global__ void k_quality_labels(const int32_t* __restrict__ q, int n, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)(q[i] - 1) / 99.0f;
+}
+
 __global__ void k_feat_norm(const float* __restrict__ feats, int n, float* __restrict__ mean,
                             float* __restrict__ stdv) {
     const int i = threadIdx.x;
@@ -260,6 +267,14 @@ dct_status dct_mlp_forward(const dct_mlp* net, const float* feats, int n, float*
     if (!feats || n < 1) return fail(DCT_ERR_INVALID_ARG, "feats null or n < 1");
     cudaError_t e = launch_mlp_forward(net, feats, n, y_out, quality_out, (cudaStream_t)stream);
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "forward launch");
+}
+
+dct_status dct_mlp_labels(const int32_t* quality, int n, float* labels_out, dct_stream_t stream) {
+    if (!quality || !labels_out) return fail(DCT_ERR_INVALID_ARG, "null pointer");
+    if (n < 1) return fail(DCT_ERR_INVALID_ARG, "n must be >= 1");
+    k_quality_labels<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(quality, n, labels_out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DCT_OK : cuda_fail(e, "labels launch");
 }
 
 size_t dct_mlp_workspace_bytes(int batch) {

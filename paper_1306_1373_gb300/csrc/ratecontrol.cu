@@ -51,6 +51,8 @@ struct RcState {
     int32_t* d_lo = nullptr;      // per slot frame bisection state
     int32_t* d_hi = nullptr;
     int32_t* d_mid = nullptr;
+    int32_t* d_rej = nullptr;     // last rejected quality (0: none) and its SSE
+    unsigned long long* d_rej_sse = nullptr;
     unsigned long long* d_fsse = nullptr;
     unsigned int* d_counter = nullptr;   // tile counter of the SSE passes
     // pinned host staging
@@ -102,11 +104,12 @@ __global__ void k_rc_decide(const unsigned long long* __restrict__ fsse, const u
     fell[f] = (s >= blo[f] && s <= bhi[f]) ? 0 : 1;
 }
 
-__global__ void k_bisect_init(int32_t* lo, int32_t* hi, int n) {
+__global__ void k_bisect_init(int32_t* lo, int32_t* hi, int32_t* rej, int n) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f < n) {
         lo[f] = 1;
         hi[f] = 100;
+        rej[f] = 0;
     }
 }
 
@@ -117,20 +120,37 @@ __global__ void k_bisect_mid(const int32_t* __restrict__ lo, const int32_t* __re
 
 __global__ void k_bisect_update(const unsigned long long* __restrict__ fsse, const int32_t* __restrict__ frame,
                                 const unsigned long long* __restrict__ thr, const int32_t* __restrict__ mid,
-                                int32_t* lo, int32_t* hi, int n) {
+                                int32_t* lo, int32_t* hi, int32_t* rej, unsigned long long* rej_sse, int n) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n) return;
-    if (fsse[f] <= thr[frame[f]]) hi[f] = mid[f];
-    else lo[f] = mid[f] + 1;
+    if (fsse[f] <= thr[frame[f]]) {
+        hi[f] = mid[f];
+    } else {
+        lo[f] = mid[f] + 1;
+        rej[f] = mid[f];
+        rej_sse[f] = fsse[f];
+    }
 }
 
-// results of the last step (its mid is the final quality) to the global arrays
+// Results to the global arrays.  The last step's mid is Q*; when its PSNR
+// lies outside the +-0.25 dB band but the last rejected quality (Q* - 1
+// whenever a step rejected) lies inside it, that quality is the result.
 __global__ void k_bisect_finish(const unsigned long long* __restrict__ fsse, const int32_t* __restrict__ frame,
-                                const int32_t* __restrict__ mid, int n, int32_t* q, unsigned long long* sse) {
+                                const int32_t* __restrict__ mid, const int32_t* __restrict__ rej,
+                                const unsigned long long* __restrict__ rej_sse, const unsigned long long* __restrict__ blo,
+                                const unsigned long long* __restrict__ bhi, int n, int32_t* q, unsigned long long* sse) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n) return;
-    q[frame[f]] = mid[f];
-    sse[frame[f]] = fsse[f];
+    const int g = frame[f];
+    int qq = mid[f];
+    unsigned long long s = fsse[f];
+    const bool in_band = s >= blo[g] && s <= bhi[g];
+    if (!in_band && rej[f] > 0 && rej_sse[f] >= blo[g] && rej_sse[f] <= bhi[g]) {
+        qq = rej[f];
+        s = rej_sse[f];
+    }
+    q[g] = qq;
+    sse[g] = s;
 }
 
 // clears the statistics words of the luma list (min words to all ones)
@@ -160,7 +180,8 @@ static void release_rc(RcState* r) {
     free_list(r->luma);
     free_list(r->sub);
     void* dev[] = {r->d_item_sse, r->d_stats, r->d_feats, r->d_target, r->d_w, r->d_h, r->d_q, r->d_sse,
-                   r->d_fell, r->d_thr, r->d_blo, r->d_bhi, r->d_lo, r->d_hi, r->d_mid, r->d_fsse, r->d_counter};
+                   r->d_fell, r->d_thr, r->d_blo, r->d_bhi, r->d_lo, r->d_hi, r->d_mid, r->d_rej, r->d_rej_sse,
+                   r->d_fsse, r->d_counter};
     for (void* p : dev) cudaFree(p);
     void* host[] = {r->h_thr, r->h_blo, r->h_bhi, r->h_target, r->h_w, r->h_h, r->h_fell};
     for (void* p : host) cudaFreeHost(p);
@@ -170,9 +191,11 @@ static void release_rc(RcState* r) {
 }
 
 template <typename T>
-static cudaError_t dalloc(T** p, size_t n) { return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)); }
+static cudaError_t dalloc(T** p, size_t n) { return ws_malloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)); }
 template <typename T>
-static cudaError_t halloc(T** p, size_t n) { return cudaMallocHost(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)); }
+static cudaError_t halloc(T** p, size_t n) {
+    return ws_malloc_host(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
+}
 
 static cudaError_t alloc_list(WorkList& w, int cap) {
     cudaError_t e = dalloc(&w.d_items, cap);
@@ -210,6 +233,8 @@ static dct_status ensure_rc(dct_plan_t plan, cudaStream_t s) {
     if (e == cudaSuccess) e = dalloc(&r->d_lo, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_hi, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_mid, cap);
+    if (e == cudaSuccess) e = dalloc(&r->d_rej, cap);
+    if (e == cudaSuccess) e = dalloc(&r->d_rej_sse, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_fsse, cap);
     if (e == cudaSuccess) e = dalloc(&r->d_counter, 1);
     if (e == cudaSuccess) e = halloc(&r->h_thr, cap);
@@ -219,8 +244,8 @@ static dct_status ensure_rc(dct_plan_t plan, cudaStream_t s) {
     if (e == cudaSuccess) e = halloc(&r->h_w, cap);
     if (e == cudaSuccess) e = halloc(&r->h_h, cap);
     if (e == cudaSuccess) e = halloc(&r->h_fell, cap);
-    if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
-    if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+    if (e == cudaSuccess) e = ws_event_create(&r->ev0);
+    if (e == cudaSuccess) e = ws_event_create(&r->ev1);
     if (e != cudaSuccess) {
         release_rc(r);
         return fail(DCT_ERR_ALLOC, std::string("rate-control workspace: ") + cudaGetErrorString(e));
@@ -279,7 +304,7 @@ static inline int blocks_for(int n) { return (n + 127) / 128; }
 // 8-step bisection over the frames of list w; results to d_q / d_sse.
 static dct_status run_bisection(dct_plan_t plan, RcState* r, WorkList& w, int k, cudaStream_t s) {
     const int n = w.nframes;
-    k_bisect_init<<<blocks_for(n), 128, 0, s>>>(r->d_lo, r->d_hi, n);
+    k_bisect_init<<<blocks_for(n), 128, 0, s>>>(r->d_lo, r->d_hi, r->d_rej, n);
     for (int step = 0; step < kBisectSteps; ++step) {
         k_bisect_mid<<<blocks_for(n), 128, 0, s>>>(r->d_lo, r->d_hi, r->d_mid, n);
         k_rc_set_quality<<<blocks_for(w.nitems), 128, 0, s>>>(w.d_items, w.nitems, k, w.d_frame, r->d_mid, nullptr,
@@ -290,10 +315,11 @@ static dct_status run_bisection(dct_plan_t plan, RcState* r, WorkList& w, int k,
         k_rc_frame_sse<<<blocks_for(n), 128, 0, s>>>(w.d_items, n, k, r->d_fsse);
         if (step + 1 < kBisectSteps)
             k_bisect_update<<<blocks_for(n), 128, 0, s>>>(r->d_fsse, w.d_frame, r->d_thr, r->d_mid, r->d_lo, r->d_hi,
-                                                          n);
+                                                          r->d_rej, r->d_rej_sse, n);
     }
-    // after 7 steps lo == hi on 1..100, so the 8th step evaluated the result
-    k_bisect_finish<<<blocks_for(n), 128, 0, s>>>(r->d_fsse, w.d_frame, r->d_mid, n, r->d_q, r->d_sse);
+    // after 7 steps lo == hi on 1..100, so the 8th step evaluated Q*
+    k_bisect_finish<<<blocks_for(n), 128, 0, s>>>(r->d_fsse, w.d_frame, r->d_mid, r->d_rej, r->d_rej_sse, r->d_blo,
+                                                  r->d_bhi, n, r->d_q, r->d_sse);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "bisection launch");
 }
@@ -446,8 +472,11 @@ dct_status dct_rate_control(dct_plan_t plan, const dct_plane* planes, int planes
         if (quality_host) quality_host[f] = q[f];
         if (sse_host) sse_host[f] = sse[f];
         if (fell_back_host) fell_back_host[f] = r->h_fell[f];
-        if (q[f] == 100 && sse[f] > r->h_thr[f]) ++unreachable;
+        // a final PSNR outside the band comes from the bisection, which
+        // evaluated the qualities on both sides of the band (or stopped at
+        // 1 or 100): no quality lands in it while PSNR rises with quality
         if (sse[f] >= r->h_blo[f] && sse[f] <= r->h_bhi[f]) ++within;
+        else ++unreachable;
     }
     if (summary) {
         summary->frames = nframes;

@@ -4,6 +4,7 @@ sizes and pitches; every step of the codec runs in the library's kernels.
 There is no CPU fallback: without the library or a CUDA device the calls
 raise.
 """
+import contextlib
 import ctypes
 import math
 import os
@@ -97,12 +98,17 @@ _SIGNATURES = {
                                        ctypes.c_int, _P, ctypes.POINTER(dct_plane), _P, _P]),
     "dct_rgb_to_yuv420": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(dct_plane),
                                          ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), _P]),
+    "dct_compress_rgb": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, _U16P,
+                                        ctypes.c_int, _P, _P]),
     "dct_entropy_stats": (ctypes.c_int, [_P, _P, ctypes.POINTER(dct_plane), ctypes.c_int, _P, _P]),
     "dct_entropy_bits": (ctypes.c_double, [ctypes.POINTER(ctypes.c_uint64)]),
     "dct_huffman_bits": (ctypes.c_uint64, [ctypes.POINTER(ctypes.c_uint64)]),
     "dct_psnr": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.POINTER(dct_plane), ctypes.c_int, _P,
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P]),
     "dct_psnr_from_sse": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double]),
+    "dct_psnr_from_sse_list": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "dct_mlp_labels": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "dct_batch_prepare": (ctypes.c_int, [_P, ctypes.POINTER(dct_batch_item), ctypes.c_int, ctypes.c_uint32, _P,
                                          ctypes.POINTER(dct_launch_shape), _P]),
     "dct_batch_launch": (ctypes.c_int, [_P, _P]),
@@ -123,38 +129,60 @@ _SIGNATURES = {
     "dct_rate_features": (ctypes.c_int, [_P, ctypes.POINTER(dct_plane), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_float), _P, _P]),
     "dct_batch_run_noalloc": (ctypes.c_int, [ctypes.POINTER(dct_batch_item), ctypes.c_int, ctypes.c_uint32, _P, _P]),
+    "dct_int_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), _P]),
+    "dct_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "dct_last_error": (ctypes.c_char_p, []),
 }
 
-_LIB = None
+_LIBS = {}
+_ACTIVE_N = None     # CORDIC count of the library the calls below use (None: the spec's)
 
 
-def load(build_if_needed=True):
-    """Loads (building first if needed) the in-tree libdctgb.so."""
-    global _LIB
-    if _LIB is not None:
-        return _LIB
-    path = _build.LIB
-    if build_if_needed and not _build.up_to_date():
-        path = _build.build()
+def load(build_if_needed=True, n=None):
+    """Loads (building first if needed) the in-tree libdctgb.so, or with n
+    the same library compiled at CORDIC iteration count n.  Without n it
+    returns the library selected by ``cordic_variant`` (default: the spec's)."""
+    n = _ACTIVE_N if n is None else n
+    key = _build.lib_path(n)
+    if key in _LIBS:
+        return _LIBS[key]
+    path = key
+    if build_if_needed and not _build.up_to_date(n):
+        path = _build.build(n=n)
     if not os.path.exists(path):
-        raise RuntimeError("libdctgb.so is missing; run paper_1306_1373_gb300.build.build()")
+        raise RuntimeError("%s is missing; run paper_1306_1373_gb300.build.build()" % path)
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _LIB = lib
+    _LIBS[key] = lib
     return lib
+
+
+@contextlib.contextmanager
+def cordic_variant(n):
+    """Within the block every call of this module goes to the library
+    compiled at CORDIC iteration count n.  Plans are tied to the library
+    that created them: create and use them inside the same block."""
+    global _ACTIVE_N
+    old = _ACTIVE_N
+    lib = load(n=n)
+    _ACTIVE_N = n
+    try:
+        yield lib
+    finally:
+        _ACTIVE_N = old
 
 
 def declared_symbols():
     return list(_SIGNATURES)
 
 
-def _check(status):
+def _check(status, lib=None):
     if status != DCT_OK:
-        raise DctError(status, load().dct_last_error().decode())
+        raise DctError(status, (lib or load()).dct_last_error().decode())
 
 
 def _stream_ptr(stream):
@@ -249,14 +277,15 @@ class Plan:
 
     def __init__(self, max_width, max_height, layout=DCT_LAYOUT_GRAY8, max_batch=0, stream=None):
         self.handle = ctypes.c_void_p()
+        self.lib = load()          # the library (CORDIC variant) that owns this plan
         desc = dct_plan_desc(int(max_width), int(max_height), int(layout), int(max_batch), 0)
-        _check(load().dct_plan_create(ctypes.byref(self.handle), ctypes.byref(desc), _stream_ptr(stream)))
+        _check(self.lib.dct_plan_create(ctypes.byref(self.handle), ctypes.byref(desc), _stream_ptr(stream)))
         self.layout = layout
         self._keep = None
 
     def close(self):
         if self.handle:
-            _check(load().dct_plan_destroy(self.handle))
+            _check(self.lib.dct_plan_destroy(self.handle))
             self.handle = ctypes.c_void_p()
 
     def __enter__(self):
@@ -289,7 +318,7 @@ def dct_compress(plan, planes, quality, qtab=None, coeffs=None, stats=None, stre
         coeffs = torch.empty(coeff_count(shapes), dtype=torch.int16, device=planes[0].device)
     _require_cuda(coeffs, stats)
     qa, n = _qtab(qtab)
-    _check(load().dct_compress(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
+    _check(plan.lib.dct_compress(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                ctypes.c_void_p(coeffs.data_ptr()),
                                ctypes.c_void_p(stats.data_ptr()) if stats is not None else None,
                                _stream_ptr(stream)))
@@ -307,7 +336,7 @@ def dct_reconstruct(plan, coeffs, out_planes, quality, qtab=None, ref_planes=Non
         refs = _planes(ref_planes)
         if sse is None:
             sse = torch.empty(len(out_planes), dtype=torch.int64, device=coeffs.device)
-    _check(load().dct_reconstruct(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), _planes(out_planes),
+    _check(plan.lib.dct_reconstruct(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), _planes(out_planes),
                                   len(out_planes), int(quality), _u16p(qa), n, refs,
                                   ctypes.c_void_p(sse.data_ptr()) if sse is not None else None,
                                   _stream_ptr(stream)))
@@ -321,7 +350,7 @@ def dct_codec_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
         sse = torch.empty(len(planes), dtype=torch.int64, device=planes[0].device)
     _require_cuda(sse, coeffs)
     qa, n = _qtab(qtab)
-    _check(load().dct_codec_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
+    _check(plan.lib.dct_codec_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                   ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                                   _planes(recon_planes) if recon_planes is not None else None,
                                   ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
@@ -334,7 +363,7 @@ def dct_exact_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
     if sse is None:
         sse = torch.empty(len(planes), dtype=torch.int64, device=planes[0].device)
     qa, n = _qtab(qtab)
-    _check(load().dct_exact_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
+    _check(plan.lib.dct_exact_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                   ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                                   _planes(recon_planes) if recon_planes is not None else None,
                                   ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
@@ -357,6 +386,27 @@ def dct_rgb_to_yuv420(rgb, y=None, cb=None, cr=None, stream=None):
     return y, cb, cr
 
 
+def rgb_coeff_count(height, width):
+    """int16 codes dct_compress_rgb writes for an RGB frame: Y, Cb, Cr."""
+    ch, cw = (height + 1) // 2, (width + 1) // 2
+    return coeff_count([(height, width), (ch, cw), (ch, cw)])
+
+
+def dct_compress_rgb(plan, rgb, quality, qtab=None, coeffs=None, stream=None):
+    """(H, W, 3) uint8 CUDA tensor (rows may be padded) -> int16 codes of its
+    Y, Cb and Cr planes (4:2:0), converted and coded in one pass."""
+    if rgb.dtype != torch.uint8 or rgb.dim() != 3 or rgb.shape[2] != 3 or rgb.stride(2) != 1 or rgb.stride(1) != 3:
+        raise ValueError("rgb must be an (H, W, 3) uint8 tensor with interleaved channels")
+    _require_cuda(rgb, coeffs)
+    h, w = rgb.shape[:2]
+    if coeffs is None:
+        coeffs = torch.empty(rgb_coeff_count(h, w), dtype=torch.int16, device=rgb.device)
+    qa, n = _qtab(qtab)
+    _check(plan.lib.dct_compress_rgb(plan.handle, ctypes.c_void_p(rgb.data_ptr()), w, h, rgb.stride(0), int(quality),
+                                     _u16p(qa), n, ctypes.c_void_p(coeffs.data_ptr()), _stream_ptr(stream)))
+    return coeffs
+
+
 DCT_ENTROPY_WORDS = 274
 
 
@@ -366,7 +416,7 @@ def dct_entropy_stats(plan, coeffs, shapes, stream=None):
     n = len(shapes)
     arr = (dct_plane * n)(*[dct_plane(None, w, h, w) for h, w in shapes])
     out = torch.empty(n, DCT_ENTROPY_WORDS, dtype=torch.int64, device=coeffs.device)
-    _check(load().dct_entropy_stats(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), arr, n,
+    _check(plan.lib.dct_entropy_stats(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), arr, n,
                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
@@ -390,7 +440,7 @@ def dct_psnr(plan, a_planes, b_planes, max_value=0.0, sse=None, host=True, strea
     if sse is None:
         sse = torch.empty(len(a_planes), dtype=torch.int64, device=a_planes[0].device)
     out = (ctypes.c_double * (len(a_planes) + 1))() if host else None
-    _check(load().dct_psnr(plan.handle, _planes(a_planes), _planes(b_planes), len(a_planes),
+    _check(plan.lib.dct_psnr(plan.handle, _planes(a_planes), _planes(b_planes), len(a_planes),
                            ctypes.c_void_p(sse.data_ptr()), out, float(max_value), _stream_ptr(stream)))
     return sse, (list(out) if host else None)
 
@@ -420,14 +470,14 @@ def make_batch_items(srcs, qualities, coeffs=None, recons=None, chroma=None, qta
 def dct_batch_prepare(plan, items, ops, sse=None, shape=None, stream=None):
     arr, keep = items
     sh = dct_launch_shape(*shape) if shape is not None else None
-    _check(load().dct_batch_prepare(plan.handle, arr, len(arr), int(ops),
+    _check(plan.lib.dct_batch_prepare(plan.handle, arr, len(arr), int(ops),
                                     ctypes.c_void_p(sse.data_ptr()) if sse is not None else None,
                                     ctypes.byref(sh) if sh is not None else None, _stream_ptr(stream)))
     plan._keep = (arr, keep, sse)
 
 
 def dct_batch_launch(plan, stream=None):
-    _check(load().dct_batch_launch(plan.handle, _stream_ptr(stream)))
+    _check(plan.lib.dct_batch_launch(plan.handle, _stream_ptr(stream)))
 
 
 def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
@@ -439,12 +489,29 @@ def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
                                         _stream_ptr(stream)))
 
 
+def dct_int_peak(kind=1, iters=4096, stream=None):
+    """Integer issue-rate probe: (ops per clock per SM, Tops/s, ms) for the
+    CORDIC micro-rotation in instruction form ``kind`` (0, 1 or 2)."""
+    opc, tops, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_float()
+    _check(load().dct_int_peak(int(kind), int(iters), ctypes.byref(opc), ctypes.byref(tops), ctypes.byref(ms),
+                               _stream_ptr(stream)))
+    return opc.value, tops.value, ms.value
+
+
+def dct_debug_fail_alloc(nth):
+    """Arms (nth >= 1) or disarms (0) the allocation-failure hook of the
+    active library; returns the allocation attempts counted so far."""
+    att = ctypes.c_int64()
+    _check(load().dct_debug_fail_alloc(int(nth), ctypes.byref(att)))
+    return att.value
+
+
 def dct_autotune(plan, stream=None):
     """Times candidate launch shapes for the prepared batch; returns
     ((threads, ctas_per_sm, tile_blocks, lanes_per_block), best ms)."""
     sh = dct_launch_shape()
     ms = ctypes.c_float()
-    _check(load().dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)))
+    _check(plan.lib.dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)))
     return (sh.threads_per_cta, sh.ctas_per_sm, sh.tile_blocks, sh.lanes_per_block), ms.value
 
 
@@ -477,12 +544,20 @@ def autotune_cached(plan, items, ops, sse=None, cache_path=None, key=None, strea
     return shape
 
 
+def dct_psnr_from_sse_list(sse_values, sample_counts, max_value=0.0):
+    """Per-plane PSNRs and the sample-weighted PSNR over all planes (a list
+    of n + 1 floats), from host SSE values and sample counts."""
+    n = len(sse_values)
+    s = (ctypes.c_uint64 * n)(*[int(v) for v in sse_values])
+    c = (ctypes.c_int64 * n)(*[int(v) for v in sample_counts])
+    out = (ctypes.c_double * (n + 1))()
+    _check(load().dct_psnr_from_sse_list(s, c, n, float(max_value), out))
+    return list(out)
+
+
 def psnr_list_from_sse(sse_values, shapes, max_value=0.0):
-    out = [dct_psnr_from_sse(int(s), h * w, max_value) for s, (h, w) in zip(sse_values, shapes)]
-    tot = sum(int(s) for s in sse_values)
-    n = sum(h * w for h, w in shapes)
-    out.append(dct_psnr_from_sse(tot, n, max_value))
-    return out
+    """dct_psnr_from_sse_list for planes of the given (height, width) shapes."""
+    return dct_psnr_from_sse_list(sse_values, [h * w for h, w in shapes], max_value)
 
 
 # ---------------------------------------------------------------------------
@@ -553,6 +628,15 @@ class Mlp:
         return losses
 
 
+def dct_mlp_labels(quality, stream=None):
+    """Device float32 training targets (Q - 1) / 99 of a device int32 tensor of qualities."""
+    _require_cuda(quality)
+    q = quality.to(torch.int32).contiguous()
+    out = torch.empty(q.numel(), dtype=torch.float32, device=q.device)
+    _check(load().dct_mlp_labels(_vp(q), int(q.numel()), _vp(out), _stream_ptr(stream)))
+    return out
+
+
 def dct_features(stats, width, height, target, stream=None):
     n = int(width.numel())
     out = torch.empty(n, DCT_MLP_INPUTS, dtype=torch.float32, device=stats.device)
@@ -566,7 +650,7 @@ def dct_rate_features(plan, planes, planes_per_frame, targets, stream=None):
     nf = len(planes) // planes_per_frame
     t = (ctypes.c_float * nf)(*[float(v) for v in targets])
     out = torch.empty(nf, DCT_MLP_INPUTS, dtype=torch.float32, device=planes[0].device)
-    _check(load().dct_rate_features(plan.handle, _planes(planes), int(planes_per_frame), nf, t, _vp(out),
+    _check(plan.lib.dct_rate_features(plan.handle, _planes(planes), int(planes_per_frame), nf, t, _vp(out),
                                     _stream_ptr(stream)))
     return out
 
@@ -580,7 +664,7 @@ def dct_rate_control(plan, planes, planes_per_frame, targets, net=None, stream=N
     sse = np.zeros(nf, dtype=np.uint64)
     fell = np.zeros(nf, dtype=np.uint8)
     summ = dct_rc_summary()
-    _check(load().dct_rate_control(plan.handle, _planes(planes), int(planes_per_frame), nf, t,
+    _check(plan.lib.dct_rate_control(plan.handle, _planes(planes), int(planes_per_frame), nf, t,
                                    ctypes.byref(net.c) if net is not None else None,
                                    q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    sse.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),

@@ -44,7 +44,7 @@ def train_network(feats, qualities, epochs=300, batch=256, lr=2e-3, seed=0, act_
     n = int(feats.shape[0])
     net = D.Mlp(init_params(seed), act_bf16=act_bf16, device=dev)
     net.set_norm(feats)
-    labels = torch.as_tensor((np.asarray(qualities, dtype=np.float32) - 1.0) / 99.0).to(dev)
+    labels = D.dct_mlp_labels(torch.as_tensor(np.asarray(qualities, dtype=np.int32)).to(dev))
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     hist = []
     for e in range(epochs):

@@ -125,10 +125,42 @@ def test_bisection_matches_oracle_grey(D):
         res = D.dct_rate_control(plan, [torch.from_numpy(i).cuda() for i in imgs], 1, targets)
     for k, img in enumerate(imgs):
         curve = sse_curve([img], luma)
-        q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], img.size)
+        q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], img.size, band_tol=0.25)
         assert int(res["quality"][k]) == q and int(res["sse"][k]) == s, k
     assert res["fell_back"].all()
     assert res["summary"]["passes"] == 8 * len(imgs)
+
+
+def test_bisection_band_pick_and_outcome_counts(D):
+    """Targets spread over 24..50 dB on small images: the library's quality
+    and SSE follow the oracle's band pick, its within / unreachable counts
+    follow the oracle's outcome split, and on images whose SSE falls as the
+    quality rises every 'unreachable' frame has no quality in the band."""
+    imgs = images(4, seed=12, lo=24, hi=56)
+    targets = list(np.linspace(24.0, 50.0, 27))
+    frames = [imgs[k % len(imgs)] for k in range(len(targets))]
+    curves = [sse_curve([img], luma) for img in imgs]
+    with D.Plan(64, 64, max_batch=32) as plan:
+        res = D.dct_rate_control(plan, [torch.from_numpy(i).cuda() for i in frames], 1, targets)
+    within = unreachable = 0
+    for k, img in enumerate(frames):
+        curve = curves[k % len(imgs)]
+        n = img.size
+        q, s, seen = ratecontrol.bisect_quality(curve.__getitem__, targets[k], n, band_tol=0.25)
+        assert int(res["quality"][k]) == q and int(res["sse"][k]) == s, k
+        qs, _, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], n)
+        out = ratecontrol.band_outcome(q, s, qs - 1 if qs - 1 in seen else None,
+                                       curve.get(qs - 1), targets[k], n)
+        assert out in ("within", "unreachable")
+        within += out == "within"
+        unreachable += out == "unreachable"
+        lo, hi = ratecontrol.sse_band(targets[k], n)
+        mono = all(curve[j + 1] <= curve[j] for j in range(1, 100))
+        if out == "unreachable" and mono:
+            assert not any(lo <= curve[j] <= hi for j in range(1, 101)), k
+    summ = res["summary"]
+    assert summ["within_tol"] == within and summ["unreachable"] == unreachable
+    assert within + unreachable == len(frames) and within > 0
 
 
 def test_bisection_matches_oracle_yuv420(D):
@@ -141,7 +173,7 @@ def test_bisection_matches_oracle_yuv420(D):
         ps = [p.numpy() for p in fr]
         curve = sse_curve(ps, luma)
         n = sum(p.size for p in ps)
-        q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], n)
+        q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], n, band_tol=0.25)
         assert int(res["quality"][k]) == q and int(res["sse"][k]) == s
 
 
@@ -163,7 +195,7 @@ def test_learned_decisions_match_oracle(D):
         if keep:
             assert int(res["quality"][k]) == int(qpred[k]) and int(res["sse"][k]) == curve[int(qpred[k])]
         else:
-            q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], img.size)
+            q, s, _ = ratecontrol.bisect_quality(curve.__getitem__, targets[k], img.size, band_tol=0.25)
             assert int(res["quality"][k]) == q and int(res["sse"][k]) == s
     s = res["summary"]
     assert s["passes"] == len(imgs) + 8 * s["fell_back"]
@@ -185,7 +217,8 @@ def test_trained_network_beats_bisection(D):
     with D.Plan(320, 320, max_batch=n_tr + n_ev) as plan:
         tr = D.dct_rate_control(plan, imgs[:n_tr], 1, targets[:n_tr])
         feats = D.dct_rate_features(plan, imgs, 1, targets)
-        labels = torch.from_numpy(((tr["quality"].astype(np.float32) - 1) / 99.0)).to(dev)
+        labels = D.dct_mlp_labels(torch.from_numpy(tr["quality"].astype(np.int32)).to(dev))
+        assert torch.equal(labels.cpu(), torch.from_numpy((tr["quality"].astype(np.float32) - 1) / 99.0))
         net = D.Mlp(mlp.init_params(10), act_bf16=True)
         ftr = feats[:n_tr].contiguous()
         net.set_norm(ftr)

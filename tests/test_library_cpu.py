@@ -133,3 +133,76 @@ def test_huffman_bits_host_function_matches_the_oracle():
     words[272] = 99
     assert D.dct_huffman_bits(words) == 99 + entropy.code_cost([5, 0, 7]) + entropy.code_cost(fib)
     assert D.dct_huffman_bits(np.zeros(274, dtype=np.uint64)) == 0
+
+
+def _noalloc_items(D, specs):
+    """dct_batch_item array from (width, height, pitch, coeffs, recon, recon_pitch, quality) tuples; the
+    pointers are fake addresses that are never dereferenced (every case below fails validation)."""
+    arr = (D.dct_batch_item * len(specs))()
+    for it, (w, h, pitch, coef, rec, rpitch, q) in zip(arr, specs):
+        it.src = D.dct_plane(0x10000, w, h, pitch)
+        it.coeffs = coef
+        it.recon = rec
+        it.recon_pitch = rpitch
+        it.quality = q
+    return arr
+
+
+@pytest.mark.parametrize("case", ["area_2p31", "width", "coef_align", "recon_pitch", "quality", "n65",
+                                  "two_pass_alone", "sse_out", "ops"])
+def test_noalloc_refuses_on_the_host_what_a_plan_refuses(lib, case):
+    """dct_batch_run_noalloc validates every item before its first CUDA call,
+    against the same limits as dct_plan_create / dct_batch_prepare (at most
+    65536 x 65536 and below 2^31 samples per plane).  Refusals therefore
+    need no GPU and enqueue nothing."""
+    import ctypes
+    from paper_1306_1373_gb300 import dctgb as D
+    C, R, S, T = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE, D.DCT_OP_TWO_PASS
+    ok = (64, 64, 64, 0x20000, 0x30000, 64, 50)
+    specs, ops, sse = [ok], C | R, None
+    if case == "area_2p31":
+        specs = [ok, (65536, 32769, 65536, 0x20000, 0x30000, 65536, 50)]
+    elif case == "width":
+        specs = [(65537, 8, 65537, 0x20000, 0x30000, 65537, 50)]
+    elif case == "coef_align":
+        specs = [(64, 64, 64, 0x20008, 0x30000, 64, 50)]
+    elif case == "recon_pitch":
+        specs = [(64, 64, 64, 0x20000, 0x30000, 63, 50)]
+    elif case == "quality":
+        specs = [(64, 64, 64, 0x20000, 0x30000, 64, 101)]
+    elif case == "n65":
+        specs = [ok] * 65
+    elif case == "two_pass_alone":
+        ops = C | T
+    elif case == "sse_out":
+        ops = C | S
+    elif case == "ops":
+        ops = 16
+    arr = _noalloc_items(D, specs)
+    st = lib.dct_batch_run_noalloc(arr, len(specs), ops, ctypes.c_void_p(sse), None)
+    assert st == 1, (case, st, lib.dct_last_error())
+
+
+def test_psnr_from_sse_list_is_the_sample_weighted_eq23(lib):
+    """Per-plane Eq. 23 values plus one PSNR over the union of the samples
+    (total SSE over total count), e.g. a 4:2:0 frame's combined figure."""
+    from paper_1306_1373_gb300 import dctgb as D
+    out = D.dct_psnr_from_sse_list([600, 0, 25], [600, 150, 150])
+    assert abs(out[0] - 20 * math.log10(255)) < 1e-12 and out[1] == math.inf
+    assert abs(out[2] - 10 * math.log10(255 ** 2 * 150 / 25)) < 1e-12
+    assert abs(out[3] - 10 * math.log10(255 ** 2 * 900 / 625)) < 1e-12
+    assert D.psnr_list_from_sse([10, 20], [(4, 5), (2, 5)], 100.0)[2] == D.dct_psnr_from_sse(30, 30, 100.0)
+    with pytest.raises(D.DctError):
+        D.dct_psnr_from_sse_list([1], [0])
+
+
+def test_fault_injection_hook_is_host_only(lib):
+    """dct_debug_fail_alloc arms and disarms without touching the GPU and
+    counts attempts monotonically; a negative count is refused."""
+    from paper_1306_1373_gb300 import dctgb as D
+    a0 = D.dct_debug_fail_alloc(3)
+    a1 = D.dct_debug_fail_alloc(0)
+    assert a1 == a0 >= 0
+    with pytest.raises(D.DctError) as ei:
+        D.dct_debug_fail_alloc(-1)
+    assert ei.value.status == 1

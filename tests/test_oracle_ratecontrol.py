@@ -157,3 +157,83 @@ def test_bisection_extremes():
     assert q == 1
     q, _, _ = ratecontrol.bisect_quality(lambda k: 10 ** 9, 20.0, 100)
     assert q == 100
+
+
+def _band_quals(curve, t, n, tol=0.25):
+    lo, hi = ratecontrol.sse_band(t, n, tol)
+    return [k for k in range(1, 101) if lo <= curve[k] <= hi]
+
+
+def _outcome_of(curve, t, n):
+    q, s, seen = ratecontrol.bisect_quality(curve.__getitem__, t, n, band_tol=0.25)
+    qs, _, _ = ratecontrol.bisect_quality(curve.__getitem__, t, n)
+    below = qs - 1 if (qs - 1) in seen else None
+    out = ratecontrol.band_outcome(q, s, below, curve[below] if below else None, t, n)
+    return q, s, qs, out
+
+
+def test_band_pick_and_outcomes_against_the_full_curve():
+    """For every target the band pick returns an evaluated quality; it is in
+    the band whenever Q* or Q* - 1 is; 'unreachable' means no quality of
+    1..100 lands in the band (on curves where PSNR rises with quality); an
+    out-of-band result with some in-band quality is 'missed'."""
+    from synth import powerlaw_image
+    checked = 0
+    for seed, (h, w) in ((8, (48, 64)), (9, (40, 40)), (10, (24, 72))):
+        img = powerlaw_image(h, w, seed=seed, beta=1.0 + seed % 3).numpy()
+        curve = _sse_curve(img)
+        n = img.size
+        mono = all(curve[k + 1] <= curve[k] for k in range(1, 100))
+        for t in np.linspace(22.0, 52.0, 121):
+            q, s, qs, out = _outcome_of(curve, t, n)
+            lo, hi = ratecontrol.sse_band(t, n)
+            inband = _band_quals(curve, t, n)
+            assert s == curve[q]
+            assert q in (qs, qs - 1)
+            if lo <= curve[qs] <= hi or (qs > 1 and lo <= curve[qs - 1] <= hi and curve[qs] > hi or
+                                         qs > 1 and lo <= curve[qs - 1] <= hi and curve[qs] < lo):
+                assert out == "within", (seed, t)
+            if out == "within":
+                assert lo <= s <= hi
+            if out == "unreachable" and mono:
+                assert inband == [], (seed, t)
+            assert out in ("within", "unreachable")
+            if out != "within" and inband:
+                assert not mono, (seed, t)
+            checked += 1
+    assert checked == 363
+
+
+def test_band_outcome_edge_cases_on_constructed_curves():
+    n = 4096
+    t = 35.0
+    lo, hi = ratecontrol.sse_band(t, n)
+    thr = ratecontrol.sse_at_most(t, n)
+    # quality 1 already far above the band: unreachable from above
+    curve = {k: max(1, lo // 4 - k) for k in range(1, 101)}
+    q, s, qs, out = _outcome_of(curve, t, n)
+    assert q == 1 and out == "unreachable"
+    # quality 100 still far below the band: unreachable from below
+    curve = {k: 10 * hi + 100 - k for k in range(1, 101)}
+    q, s, qs, out = _outcome_of(curve, t, n)
+    assert q == 100 and out == "unreachable"
+    # the band falls between two adjacent qualities
+    curve = {k: (2 * hi if k < 60 else lo // 2) for k in range(1, 101)}
+    q, s, qs, out = _outcome_of(curve, t, n)
+    assert qs == 60 and q == 60 and out == "unreachable"
+    # Q* overshoots the band but Q* - 1 sits just below the target: the band pick takes Q* - 1
+    curve = {k: (thr + 1 if k < 60 else lo // 2) for k in range(1, 101)}
+    q, s, qs, out = _outcome_of(curve, t, n)
+    assert qs == 60 and q == 59 and out == "within" and s == thr + 1 <= hi
+    # the split rests on PSNR rising with quality: an in-band quality far
+    # from the bracket (a non-monotone curve) is invisible to it
+    curve = {k: (2 * hi if k < 60 else lo // 2) for k in range(1, 101)}
+    curve[20] = thr
+    q, s, qs, out = _outcome_of(curve, t, n)
+    assert out == "unreachable" and _band_quals(curve, t, n) == [20]
+    # a bisection that ends at Q* > 1 has evaluated Q* - 1, so after the band
+    # pick every out-of-band result is bracketed: 'missed' is only reachable
+    # for a quality chosen some other way (the band_outcome rule itself)
+    assert ratecontrol.band_outcome(60, lo // 2, None, None, t, n) == "missed"
+    assert ratecontrol.band_outcome(60, lo // 2, 58, 2 * hi, t, n) == "missed"
+    assert ratecontrol.band_outcome(60, lo // 2, 59, hi, t, n) == "missed"      # 59 itself in the band
