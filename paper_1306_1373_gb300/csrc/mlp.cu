@@ -161,8 +161,6 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __re
     P[p] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
 }
 
-// mean and standard deviation of every feature (one thread per feature, in
-// row order, float64); a standard deviation below 1e-6 becomes 1
 // training target of a quality label: (Q - 1) / 99 (IEEE division, as the
 // host would compute it in float32)
 __global__ void k_quality_labels(const int32_t* __restrict__ q, int n, float* __restrict__ out) {
@@ -170,6 +168,8 @@ __global__ void k_quality_labels(const int32_t* __restrict__ q, int n, float* __
     if (i < n) out[i] = (float)(q[i] - 1) / 99.0f;
 }
 
+// mean and standard deviation of every feature (one thread per feature, in
+// row order, float64); a standard deviation below 1e-6 becomes 1
 __global__ void k_feat_norm(const float* __restrict__ feats, int n, float* __restrict__ mean,
                             float* __restrict__ stdv) {
     const int i = threadIdx.x;

@@ -30,7 +30,9 @@ constexpr int kRgbUnitW = 16 * kRgbMbPerUnit;       // 256 pixels
 constexpr int kRgbThreads = 96;                     // one thread per block: 64 Y + 16 Cb + 16 Cr
 constexpr int kRgbYBytes = 16 * kRgbUnitW;          // 16 rows x 256 luma samples
 constexpr int kRgbCBytes = 8 * (kRgbUnitW / 2);     // 8 rows x 128 chroma samples
-constexpr int kRgbSmem = 2 * (int)sizeof(QuantSet) + kRgbYBytes + 2 * kRgbCBytes + kRgbThreads * 128;
+constexpr int kRgbRawRow = 3 * kRgbUnitW + 32;       // one strip row of RGB bytes, from its aligned 16-byte chunk
+constexpr int kRgbSmem = 2 * (int)sizeof(QuantSet) + kRgbYBytes + 2 * kRgbCBytes + kRgbThreads * 128 +
+                         16 * kRgbRawRow + 16 * 4;
 
 struct RgbArgs {
     const uint8_t* rgb;
@@ -44,8 +46,8 @@ struct RgbArgs {
     int64_t cb_offset, cr_offset;  // element offsets of the Cb and Cr codes
 };
 
-__device__ __forceinline__ void rgb_convert(const uint8_t* __restrict__ p, int& y, int& cb, int& cr) {
-    const int r = __ldg(p), g = __ldg(p + 1), b = __ldg(p + 2);
+__device__ __forceinline__ void rgb_convert(const uint8_t* p, int& y, int& cb, int& cr) {
+    const int r = p[0], g = p[1], b = p[2];
     y = (19595 * r + 38470 * g + 7471 * b + 32768) >> 16;
     cb = max(0, min(255, (-11058 * r - 21710 * g + 32768 * b + (128 << 16) + 32768) >> 16));
     cr = max(0, min(255, (32768 * r - 27439 * g - 5329 * b + (128 << 16) + 32768) >> 16));
@@ -72,13 +74,15 @@ __device__ __forceinline__ void quantize_fwd(int (&x)[8][8], const QuantSet& T) 
     }
 }
 
-__global__ void __launch_bounds__(kRgbThreads) k_compress_rgb(const __grid_constant__ RgbArgs a) {
+__global__ void __launch_bounds__(kRgbThreads, 6) k_compress_rgb(const __grid_constant__ RgbArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     QuantSet* tabs = reinterpret_cast<QuantSet*>(smem);
     uint8_t* ys = smem + 2 * sizeof(QuantSet);            // [16][256]
     uint8_t* cbs = ys + kRgbYBytes;                       // [8][128]
     uint8_t* crs = cbs + kRgbCBytes;                      // [8][128]
     uint8_t* stage = crs + kRgbCBytes;                    // [96][128]
+    uint8_t* raw = stage + kRgbThreads * 128;             // [16][kRgbRawRow] RGB bytes of the strip
+    int* lead16 = reinterpret_cast<int*>(raw + 16 * kRgbRawRow);   // [16] offset of each row in its chunk
     {
         const uint32_t* s = reinterpret_cast<const uint32_t*>(a.tabs);
         uint32_t* d = reinterpret_cast<uint32_t*>(tabs);
@@ -90,20 +94,48 @@ __global__ void __launch_bounds__(kRgbThreads) k_compress_rgb(const __grid_const
         const int mx0 = (unit - my * a.units_x) * kRgbMbPerUnit;
         __syncthreads();          // the previous unit's stage is written out; tables are in place
 
+        // phase 0: the strip's 16 pixel rows (the last image row repeated
+        // below the image), columns x0 .. x1 - 1, into shared memory with
+        // 16-byte cp.async copies of the aligned chunks inside each row's
+        // bytes; the partial chunks at either end are read byte by byte, so
+        // nothing outside the caller's rows is touched.  Every pixel phase
+        // 1 needs lies in these rows and columns.
+        const int x0 = 16 * mx0, x1 = min(x0 + kRgbUnitW, a.width);
+        const int nbytes = 3 * (x1 - x0);
+        if (t < 16)
+            lead16[t] = (int)((uintptr_t)(a.rgb + (size_t)min(16 * my + t, a.height - 1) * a.pitch + 3 * x0) & 15u);
+        constexpr int kChunks = kRgbRawRow / 16;
+        for (int c = t; c < 16 * kChunks; c += kRgbThreads) {
+            const int r = c / kChunks, k = c - r * kChunks;
+            const uint8_t* row = a.rgb + (size_t)min(16 * my + r, a.height - 1) * a.pitch + 3 * x0;
+            const int lead = (int)((uintptr_t)row & 15u);
+            const int b0 = 16 * k;
+            if (b0 >= lead + nbytes) continue;
+            const uint8_t* src = row - lead + b0;           // 16-byte aligned
+            uint8_t* dst = raw + r * kRgbRawRow + b0;
+            if (b0 >= lead && b0 + 16 <= lead + nbytes) {
+                cp_async16(dst, src);
+            } else {
+                for (int j = max(b0, lead); j < min(b0 + 16, lead + nbytes); ++j) dst[j - b0] = __ldg(src + (j - b0));
+            }
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+
         // phase 1: every 2x2 quad of the strip -> 4 luma samples and one
-        // chroma sample of each plane (8 x 128 quads)
+        // chroma sample of each plane (8 x 128 quads), from shared memory
         for (int q = t; q < 8 * (kRgbUnitW / 2); q += kRgbThreads) {
             const int qi = q / (kRgbUnitW / 2), qj = q - qi * (kRgbUnitW / 2);
-            const int py = 16 * my + 2 * qi, px = 16 * mx0 + 2 * qj;      // top-left pixel of the quad
             int sb = 0, sr = 0;
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-                const int yy = min(py + dy, a.height - 1);
+                const uint8_t* rr = raw + (2 * qi + dy) * kRgbRawRow + lead16[2 * qi + dy];
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
-                    const int xx = min(px + dx, a.width - 1);
+                    const int xx = min(x0 + 2 * qj + dx, a.width - 1) - x0;
                     int Y, Cb, Cr;
-                    rgb_convert(a.rgb + (size_t)yy * a.pitch + 3 * xx, Y, Cb, Cr);
+                    rgb_convert(rr + 3 * xx, Y, Cb, Cr);
                     ys[(2 * qi + dy) * kRgbUnitW + 2 * qj + dx] = (uint8_t)Y;
                     sb += Cb;
                     sr += Cr;
@@ -117,12 +149,13 @@ __global__ void __launch_bounds__(kRgbThreads) k_compress_rgb(const __grid_const
                 sb = sr = 0;
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
-                    const int yy = min(2 * cyc + dy, a.height - 1);
+                    const int ry = min(2 * cyc + dy, a.height - 1) - 16 * my;
+                    const uint8_t* rr = raw + ry * kRgbRawRow + lead16[ry];
 #pragma unroll
                     for (int dx = 0; dx < 2; ++dx) {
-                        const int xx = min(2 * cxc + dx, a.width - 1);
+                        const int xx = min(2 * cxc + dx, a.width - 1) - x0;
                         int Y, Cb, Cr;
-                        rgb_convert(a.rgb + (size_t)yy * a.pitch + 3 * xx, Y, Cb, Cr);
+                        rgb_convert(rr + 3 * xx, Y, Cb, Cr);
                         sb += Cb;
                         sr += Cr;
                     }

@@ -35,10 +35,10 @@ def attempts_of(D, fn):
 
 def test_batch_workspace_allocation_failures(D):
     srcs, quals = srcs_and_quals()
-    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    S = D.DCT_OP_SSE                       # the fused pass that stores nothing but the SSE
     ref = torch.zeros(5, dtype=torch.int64, device="cuda")
     with D.Plan(128, 128, max_batch=8) as plan:
-        k = attempts_of(D, lambda: D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), C | R | S, sse=ref))
+        k = attempts_of(D, lambda: D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), S, sse=ref))
         D.dct_batch_launch(plan)
         torch.cuda.synchronize()
     assert k == 8                        # 4 device buffers, 3 pinned buffers, 1 stream
@@ -47,14 +47,14 @@ def test_batch_workspace_allocation_failures(D):
         with D.Plan(128, 128, max_batch=8) as plan:
             D.dct_debug_fail_alloc(n)
             with pytest.raises(D.DctError) as ei:
-                D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), C | R | S, sse=sse)
+                D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), S, sse=sse)
             assert ei.value.status == 3, n
             torch.cuda.synchronize()
             assert int(sse.min()) == -1 and int(sse.max()) == -1       # nothing was enqueued
             with pytest.raises(D.DctError) as ei:
                 D.dct_batch_launch(plan)                                 # nothing prepared
             assert ei.value.status == 6
-            D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), C | R | S, sse=sse)
+            D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), S, sse=sse)
             D.dct_batch_launch(plan)
             torch.cuda.synchronize()
             assert torch.equal(sse, ref), n
@@ -62,10 +62,10 @@ def test_batch_workspace_allocation_failures(D):
 
 def test_autotune_event_failure_keeps_the_plan(D):
     srcs, quals = srcs_and_quals()
-    C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
+    S = D.DCT_OP_SSE
     sse = torch.zeros(5, dtype=torch.int64, device="cuda")
     with D.Plan(128, 128, max_batch=8) as plan:
-        D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), C | R | S, sse=sse)
+        D.dct_batch_prepare(plan, D.make_batch_items(srcs, quals), S, sse=sse)
         D.dct_batch_launch(plan)
         torch.cuda.synchronize()
         ref = sse.clone()
