@@ -227,104 +227,139 @@ class ClockSampler:
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_stripe_step(host_grey, row0, rows):
+STRIPE_ROWS = 256
+
+
+def oracle_stripe_step(plane, row0, rows, chroma):
     """Oracle compress -> reconstruct -> SSE on rows [row0, row0 + rows) of
-    the grey plane; returns the number of samples processed."""
+    one plane (chrominance table when chroma); returns the samples processed."""
     from oracle import codec, ijg, psnr
-    Q = ijg.luma_table(QUALITY)
-    stripe = host_grey[row0:row0 + rows]
+    Q = ijg.chroma_table(QUALITY) if chroma else ijg.luma_table(QUALITY)
+    stripe = plane[row0:row0 + rows]
     c = codec.compress_plane(stripe, Q)
     r = codec.reconstruct_plane(c, Q, *stripe.shape)
     psnr.sse(stripe, r)
     return stripe.size
 
 
-def cpu_baseline(host_grey, budget_s, rows=256):
-    """The oracle on one thread for about budget_s seconds."""
-    n = 0
-    stripes = 0
+def stripe_schedule(shapes, rows=STRIPE_ROWS):
+    """Every stripe of every plane of the workload once, in plane order:
+    (plane index, first row, rows).  One pass covers one benchmark step's
+    samples; the CPU legs time bounded runs along this cyclic schedule."""
+    out = []
+    for i, (h, w) in enumerate(shapes):
+        for r0 in range(0, h, rows):
+            out.append((i, r0, min(rows, h - r0)))
+    return out
+
+
+def host_workload():
+    """The benchmark planes generated on the host (same recipe and seeds as
+    make_planes; the host's random stream differs from the GPU's, the
+    sample statistics do not), with their chroma flags."""
+    from synth import powerlaw_image, yuv420_frame
+    grey = powerlaw_image(8192, 8192, seed=11, device="cpu").numpy()
+    y, cb, cr = (p.numpy() for p in yuv420_frame(3840, 2160, seed=12, device="cpu"))
+    return [grey, y, cb, cr], [False, False, True, True]
+
+
+def cpu_baseline(planes, chroma, budget_s):
+    """The oracle on one thread for about budget_s seconds along the stripe schedule."""
+    sched = stripe_schedule([p.shape for p in planes])
+    n = k = 0
     t0 = time.perf_counter()
-    row0 = 0
     while True:
-        n += oracle_stripe_step(host_grey, row0, rows)
-        stripes += 1
-        row0 = (row0 + rows) % host_grey.shape[0]
+        i, r0, rows = sched[k % len(sched)]
+        n += oracle_stripe_step(planes[i], r0, rows, chroma[i])
+        k += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt / 1e6, "unit": "MPix/s", "cores": 1, "kind": "oracle",
-            "sample": "%d stripes of %dx%d samples of the 8192x8192 grey plane (oracle: numpy, one thread), %.1f s"
-                      % (stripes, rows, host_grey.shape[1], dt)}
+            "sample": "%d stripes of up to %d rows, cycling through the grey plane and the 4:2:0 frame's Y, Cb and "
+                      "Cr planes with their own tables (oracle: numpy, one thread), %.1f s" % (k, STRIPE_ROWS, dt)}
 
 
-# Worker side of the all-cores oracle pool: the plane comes through shared
-# memory, each task is one stripe.
+# Worker side of the all-cores oracle pool: the planes come through shared
+# memory, each task is one stripe of one plane.
 _POOL = {}
 
 
-def _pool_init(shm_name, shape):
+def _pool_init(specs):
     from multiprocessing import shared_memory
     import numpy as np
-    shm = shared_memory.SharedMemory(name=shm_name)
-    _POOL["shm"] = shm
-    _POOL["plane"] = np.ndarray(shape, dtype=np.uint8, buffer=shm.buf)
-    oracle_stripe_step(_POOL["plane"], 0, 8)      # imports done before any timing
+    _POOL["shm"] = []
+    _POOL["planes"] = []
+    for name, shape, chroma in specs:
+        shm = shared_memory.SharedMemory(name=name)
+        _POOL["shm"].append(shm)
+        _POOL["planes"].append((np.ndarray(shape, dtype=np.uint8, buffer=shm.buf), chroma))
+    plane, chroma = _POOL["planes"][0]
+    oracle_stripe_step(plane, 0, 8, chroma)       # imports done before any timing
 
 
 def _pool_stripe(task):
-    row0, rows = task
-    return oracle_stripe_step(_POOL["plane"], row0, rows)
+    i, row0, rows = task
+    plane, chroma = _POOL["planes"][i]
+    return oracle_stripe_step(plane, row0, rows, chroma)
 
 
 class OraclePool:
     """The unmodified oracle run on every host core: one spawned process per
-    core, each task one stripe of rows of the plane.  Spawned (not forked)
-    so that it is safe after CUDA has been initialised."""
+    core, each task one stripe of one plane.  Spawned (not forked) so that
+    it is safe after CUDA has been initialised."""
 
-    def __init__(self, host_grey, cores=None):
+    def __init__(self, planes, chroma, cores=None):
         import multiprocessing as mp
         from multiprocessing import shared_memory
         import numpy as np
         self.cores = int(cores or len(os.sched_getaffinity(0)))
-        self.height = host_grey.shape[0]
-        self.shm = shared_memory.SharedMemory(create=True, size=host_grey.nbytes)
-        np.ndarray(host_grey.shape, dtype=np.uint8, buffer=self.shm.buf)[:] = host_grey
+        self.sched = stripe_schedule([p.shape for p in planes])
+        self.pos = 0
+        self.shms = []
+        specs = []
+        for p, c in zip(planes, chroma):
+            shm = shared_memory.SharedMemory(create=True, size=max(1, p.nbytes))
+            np.ndarray(p.shape, dtype=np.uint8, buffer=shm.buf)[:] = p
+            self.shms.append(shm)
+            specs.append((shm.name, p.shape, bool(c)))
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init,
-                                                 initargs=(self.shm.name, host_grey.shape))
-        self.pool.map(_pool_stripe, [(0, 8)] * self.cores, chunksize=1)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init, initargs=(specs,))
+        self.pool.map(_pool_stripe, [(0, 0, 8)] * self.cores, chunksize=1)
 
-    def step(self, row0, rows):
-        """One stripe per core, all at once; returns the samples processed."""
-        tasks = [((row0 + k * rows) % self.height, rows) for k in range(self.cores)]
+    def step(self):
+        """The next `cores` stripes of the schedule, one per core, all at
+        once; returns the samples processed."""
+        tasks = [self.sched[(self.pos + k) % len(self.sched)] for k in range(self.cores)]
+        self.pos = (self.pos + self.cores) % len(self.sched)
         return sum(self.pool.map(_pool_stripe, tasks, chunksize=1))
 
     def close(self):
         self.pool.close()
         self.pool.join()
-        self.shm.close()
-        self.shm.unlink()
+        for shm in self.shms:
+            shm.close()
+            shm.unlink()
 
 
-def cpu_baseline_parallel(host_grey, budget_s, rows=256, cores=None):
+def cpu_baseline_parallel(planes, chroma, budget_s, cores=None):
     """The oracle on every host core for about budget_s seconds."""
-    op = OraclePool(host_grey, cores)
+    op = OraclePool(planes, chroma, cores)
     try:
         n = steps = 0
-        row0 = 0
         t0 = time.perf_counter()
         while True:
-            n += op.step(row0, rows)
+            n += op.step()
             steps += 1
-            row0 = (row0 + op.cores * rows) % host_grey.shape[0]
             if time.perf_counter() - t0 >= budget_s:
                 break
         dt = time.perf_counter() - t0
     finally:
         op.close()
     return {"value": n / dt / 1e6, "unit": "MPix/s", "cores": op.cores, "kind": "oracle",
-            "sample": "%d stripes of %dx%d samples of the 8192x8192 grey plane (oracle: numpy, one spawned "
-                      "process per core), %.1f s" % (steps * op.cores, rows, host_grey.shape[1], dt)}
+            "sample": "%d stripes of up to %d rows, cycling through the grey plane and the 4:2:0 frame's Y, Cb and "
+                      "Cr planes with their own tables (oracle: numpy, one spawned process per core), %.1f s"
+                      % (steps * op.cores, STRIPE_ROWS, dt)}
 
 
 def run_reference(args):
@@ -332,17 +367,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from synth import powerlaw_image
-    grey = powerlaw_image(8192, 8192, seed=11, device="cpu").numpy()
-    rows = 256
-    op = OraclePool(grey)
+    planes, chroma = host_workload()
+    op = OraclePool(planes, chroma)
     try:
-        for w in range(args.warmup):
-            op.step((w * op.cores * rows) % 8192, rows)
+        for _ in range(args.warmup):
+            op.step()
         t0 = time.perf_counter()
         n = 0
-        for s in range(args.steps):
-            n += op.step((s * op.cores * rows) % 8192, rows)
+        for _ in range(args.steps):
+            n += op.step()
         dt = time.perf_counter() - t0
     finally:
         op.close()
@@ -352,10 +385,12 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD,
-                       "sample_per_step": "%d stripes of %dx8192 of the grey plane, one per core" % (op.cores, rows)},
+                       "sample_per_step": "%d stripes of up to %d rows, one per core, cycling through the grey "
+                                          "plane and the 4:2:0 frame's planes with their own tables"
+                                          % (op.cores, STRIPE_ROWS)},
             "cpu_baseline": {"value": value, "unit": "MPix/s", "cores": op.cores, "kind": "oracle",
-                             "sample": "%d steps of %d %dx8192 stripes (numpy oracle, one spawned process per core)"
-                                       % (args.steps, op.cores, rows)},
+                             "sample": "%d steps of %d stripes (numpy oracle, one spawned process per core)"
+                                       % (args.steps, op.cores)},
             "e2e": {"value": value, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -1152,9 +1187,9 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
-        host_grey = planes[0].cpu().numpy()
-        single = cpu_baseline(host_grey, args.cpu_seconds)
-        line["cpu_baseline"] = cpu_baseline_parallel(host_grey, args.cpu_seconds)
+        host_planes = [p.cpu().numpy() for p in planes]
+        single = cpu_baseline(host_planes, chroma, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline_parallel(host_planes, chroma, args.cpu_seconds)
         line["cpu_baseline"]["single_thread"] = single
     plan.close()
     if not args.no_context:

@@ -1,9 +1,9 @@
 // Learned rate controller, network side: the 80 features, input
 // normalisation, forward pass, back-propagation with deterministic
 // (fixed-order) minibatch sums, and Adam.  The network is tiny (9409
-// parameters), so it runs on plain FMA units: one thread per sample for the
-// forward and delta passes, one thread per parameter for the gradient sums
-// and the update.
+// parameters), so it runs on plain FMA units: one thread per sample for
+// inference, one warp per minibatch row for the training forward and delta
+// pass, one thread per parameter for the gradient sums and the update.
 #include <cmath>
 #include <cstring>
 
@@ -83,24 +83,80 @@ __global__ void k_mlp_forward(const float* __restrict__ P, const float* __restri
     }
 }
 
-// forward + output delta + hidden deltas of one minibatch row
+// forward + output delta + hidden deltas of one minibatch row per warp:
+// lane l owns hidden units l and l + 32 of both layers; every sum runs over
+// its inputs in ascending order as forward_sample's does (the inputs a lane
+// does not hold come by shuffle), so the cache holds the same values.
 __global__ void k_mlp_delta(const float* __restrict__ P, const float* __restrict__ feats,
                             const float* __restrict__ labels, const int* __restrict__ index,
                             const float* __restrict__ mean, const float* __restrict__ stdv, int bf16, int batch,
                             float* __restrict__ cache) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= batch) return;
+    const int lane = threadIdx.x & 31;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= batch) return;                                   // warp-uniform
     const int s = index[b];
     float* c = cache + (size_t)b * kCache;
-    const float y = forward_sample(P, feats + (size_t)s * kIn, mean, stdv, bf16, c);
-    const float dz = 2.0f * (y - labels[s]) / (float)batch * y * (1.0f - y);
-    c[cDz] = dz;
-    for (int j = 0; j < kHid; ++j) c[cDa2 + j] = dz * P[oW3 + j] * gelu_grad(c[cA2 + j]);
-    for (int i = 0; i < kHid; ++i) {
-        float s2 = 0.0f;
-        for (int j = 0; j < kHid; ++j) s2 = fmaf(c[cDa2 + j], P[oW2 + j * kHid + i], s2);
-        c[cDa1 + i] = s2 * gelu_grad(c[cA1 + i]);
+    const float* x = feats + (size_t)s * kIn;
+    float xn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = lane + 32 * k;
+        xn[k] = i < kIn ? (x[i] - mean[i]) / stdv[i] : 0.0f;
+        if (i < kIn) c[cXn + i] = xn[k];
     }
+    // layer 1
+    float a1[2], h1[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) a1[k] = P[oB1 + lane + 32 * k];
+    for (int i = 0; i < kIn; ++i) {
+        const float v = __shfl_sync(0xffffffffu, xn[i >> 5], i & 31);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) a1[k] = fmaf(P[oW1 + (lane + 32 * k) * kIn + i], v, a1[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        h1[k] = act(gelu(a1[k]), bf16);
+        c[cA1 + lane + 32 * k] = a1[k];
+        c[cH1 + lane + 32 * k] = h1[k];
+    }
+    // layer 2
+    float a2[2], h2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) a2[k] = P[oB2 + lane + 32 * k];
+    for (int i = 0; i < kHid; ++i) {
+        const float v = __shfl_sync(0xffffffffu, h1[i >> 5], i & 31);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) a2[k] = fmaf(P[oW2 + (lane + 32 * k) * kHid + i], v, a2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        h2[k] = act(gelu(a2[k]), bf16);
+        c[cA2 + lane + 32 * k] = a2[k];
+        c[cH2 + lane + 32 * k] = h2[k];
+    }
+    // output, in the same order on every lane
+    float z = P[oB3];
+    for (int j = 0; j < kHid; ++j) z = fmaf(P[oW3 + j], __shfl_sync(0xffffffffu, h2[j >> 5], j & 31), z);
+    const float y = 1.0f / (1.0f + expf(-z));
+    const float dz = 2.0f * (y - labels[s]) / (float)batch * y * (1.0f - y);
+    if (lane == 0) {
+        c[cY] = y;
+        c[cDz] = dz;
+    }
+    float da2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        da2[k] = dz * P[oW3 + lane + 32 * k] * gelu_grad(a2[k]);
+        c[cDa2 + lane + 32 * k] = da2[k];
+    }
+    float s2[2] = {0.0f, 0.0f};
+    for (int j = 0; j < kHid; ++j) {
+        const float d = __shfl_sync(0xffffffffu, da2[j >> 5], j & 31);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) s2[k] = fmaf(d, P[oW2 + j * kHid + lane + 32 * k], s2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) c[cDa1 + lane + 32 * k] = s2[k] * gelu_grad(a1[k]);
 }
 
 // one thread per parameter (plus one for the loss): sums over the minibatch
@@ -291,9 +347,11 @@ dct_status dct_mlp_loss_grad(const dct_mlp* net, const float* feats, const float
     if (batch < 1 || batch > (1 << 20)) return fail(DCT_ERR_INVALID_ARG, "batch must be 1..2^20");
     cudaStream_t s = (cudaStream_t)stream;
     float* cache = static_cast<float*>(workspace);
-    k_mlp_delta<<<(batch + 63) / 64, 64, 0, s>>>(net->params, feats, labels, index, net->feat_mean, net->feat_std,
-                                                 net->act_bf16, batch, cache);
-    k_mlp_grad<<<(kParams + 1 + 255) / 256, 256, 0, s>>>(cache, labels, index, batch, grad_out, loss_out);
+    // one warp per row (4 rows per CTA); 64-thread CTAs for the per-parameter
+    // sums so that they spread over every SM
+    k_mlp_delta<<<(batch + 3) / 4, 128, 0, s>>>(net->params, feats, labels, index, net->feat_mean, net->feat_std,
+                                                net->act_bf16, batch, cache);
+    k_mlp_grad<<<(kParams + 1 + 63) / 64, 64, 0, s>>>(cache, labels, index, batch, grad_out, loss_out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "gradient launch");
 }

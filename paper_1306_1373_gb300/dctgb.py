@@ -279,13 +279,13 @@ class Plan:
         self.handle = ctypes.c_void_p()
         self.lib = load()          # the library (CORDIC variant) that owns this plan
         desc = dct_plan_desc(int(max_width), int(max_height), int(layout), int(max_batch), 0)
-        _check(self.lib.dct_plan_create(ctypes.byref(self.handle), ctypes.byref(desc), _stream_ptr(stream)))
+        _check(self.lib.dct_plan_create(ctypes.byref(self.handle), ctypes.byref(desc), _stream_ptr(stream)), self.lib)
         self.layout = layout
         self._keep = None
 
     def close(self):
         if self.handle:
-            _check(self.lib.dct_plan_destroy(self.handle))
+            _check(self.lib.dct_plan_destroy(self.handle), self.lib)
             self.handle = ctypes.c_void_p()
 
     def __enter__(self):
@@ -321,7 +321,7 @@ def dct_compress(plan, planes, quality, qtab=None, coeffs=None, stats=None, stre
     _check(plan.lib.dct_compress(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                ctypes.c_void_p(coeffs.data_ptr()),
                                ctypes.c_void_p(stats.data_ptr()) if stats is not None else None,
-                               _stream_ptr(stream)))
+                               _stream_ptr(stream)), plan.lib)
     return coeffs
 
 
@@ -339,7 +339,7 @@ def dct_reconstruct(plan, coeffs, out_planes, quality, qtab=None, ref_planes=Non
     _check(plan.lib.dct_reconstruct(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), _planes(out_planes),
                                   len(out_planes), int(quality), _u16p(qa), n, refs,
                                   ctypes.c_void_p(sse.data_ptr()) if sse is not None else None,
-                                  _stream_ptr(stream)))
+                                  _stream_ptr(stream)), plan.lib)
     return sse
 
 
@@ -353,7 +353,7 @@ def dct_codec_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
     _check(plan.lib.dct_codec_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                   ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                                   _planes(recon_planes) if recon_planes is not None else None,
-                                  ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
+                                  ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)), plan.lib)
     return sse
 
 
@@ -366,7 +366,7 @@ def dct_exact_fused(plan, planes, quality, qtab=None, coeffs=None, recon_planes=
     _check(plan.lib.dct_exact_fused(plan.handle, _planes(planes), len(planes), int(quality), _u16p(qa), n,
                                   ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                                   _planes(recon_planes) if recon_planes is not None else None,
-                                  ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)))
+                                  ctypes.c_void_p(sse.data_ptr()), _stream_ptr(stream)), plan.lib)
     return sse
 
 
@@ -403,7 +403,7 @@ def dct_compress_rgb(plan, rgb, quality, qtab=None, coeffs=None, stream=None):
         coeffs = torch.empty(rgb_coeff_count(h, w), dtype=torch.int16, device=rgb.device)
     qa, n = _qtab(qtab)
     _check(plan.lib.dct_compress_rgb(plan.handle, ctypes.c_void_p(rgb.data_ptr()), w, h, rgb.stride(0), int(quality),
-                                     _u16p(qa), n, ctypes.c_void_p(coeffs.data_ptr()), _stream_ptr(stream)))
+                                     _u16p(qa), n, ctypes.c_void_p(coeffs.data_ptr()), _stream_ptr(stream)), plan.lib)
     return coeffs
 
 
@@ -417,7 +417,7 @@ def dct_entropy_stats(plan, coeffs, shapes, stream=None):
     arr = (dct_plane * n)(*[dct_plane(None, w, h, w) for h, w in shapes])
     out = torch.empty(n, DCT_ENTROPY_WORDS, dtype=torch.int64, device=coeffs.device)
     _check(plan.lib.dct_entropy_stats(plan.handle, ctypes.c_void_p(coeffs.data_ptr()), arr, n,
-                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), plan.lib)
     return out
 
 
@@ -441,7 +441,7 @@ def dct_psnr(plan, a_planes, b_planes, max_value=0.0, sse=None, host=True, strea
         sse = torch.empty(len(a_planes), dtype=torch.int64, device=a_planes[0].device)
     out = (ctypes.c_double * (len(a_planes) + 1))() if host else None
     _check(plan.lib.dct_psnr(plan.handle, _planes(a_planes), _planes(b_planes), len(a_planes),
-                           ctypes.c_void_p(sse.data_ptr()), out, float(max_value), _stream_ptr(stream)))
+                           ctypes.c_void_p(sse.data_ptr()), out, float(max_value), _stream_ptr(stream)), plan.lib)
     return sse, (list(out) if host else None)
 
 
@@ -472,12 +472,12 @@ def dct_batch_prepare(plan, items, ops, sse=None, shape=None, stream=None):
     sh = dct_launch_shape(*shape) if shape is not None else None
     _check(plan.lib.dct_batch_prepare(plan.handle, arr, len(arr), int(ops),
                                     ctypes.c_void_p(sse.data_ptr()) if sse is not None else None,
-                                    ctypes.byref(sh) if sh is not None else None, _stream_ptr(stream)))
+                                    ctypes.byref(sh) if sh is not None else None, _stream_ptr(stream)), plan.lib)
     plan._keep = (arr, keep, sse)
 
 
 def dct_batch_launch(plan, stream=None):
-    _check(plan.lib.dct_batch_launch(plan.handle, _stream_ptr(stream)))
+    _check(plan.lib.dct_batch_launch(plan.handle, _stream_ptr(stream)), plan.lib)
 
 
 def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
@@ -511,7 +511,7 @@ def dct_autotune(plan, stream=None):
     ((threads, ctas_per_sm, tile_blocks, lanes_per_block), best ms)."""
     sh = dct_launch_shape()
     ms = ctypes.c_float()
-    _check(plan.lib.dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)))
+    _check(plan.lib.dct_autotune(plan.handle, ctypes.byref(sh), ctypes.byref(ms), _stream_ptr(stream)), plan.lib)
     return (sh.threads_per_cta, sh.ctas_per_sm, sh.tile_blocks, sh.lanes_per_block), ms.value
 
 
@@ -651,7 +651,7 @@ def dct_rate_features(plan, planes, planes_per_frame, targets, stream=None):
     t = (ctypes.c_float * nf)(*[float(v) for v in targets])
     out = torch.empty(nf, DCT_MLP_INPUTS, dtype=torch.float32, device=planes[0].device)
     _check(plan.lib.dct_rate_features(plan.handle, _planes(planes), int(planes_per_frame), nf, t, _vp(out),
-                                    _stream_ptr(stream)))
+                                    _stream_ptr(stream)), plan.lib)
     return out
 
 
@@ -669,7 +669,7 @@ def dct_rate_control(plan, planes, planes_per_frame, targets, net=None, stream=N
                                    q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    sse.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                    fell.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(summ),
-                                   _stream_ptr(stream)))
+                                   _stream_ptr(stream)), plan.lib)
     return dict(quality=q, sse=sse, fell_back=fell,
                 summary={f: getattr(summ, f) for f, _ in dct_rc_summary._fields_})
 

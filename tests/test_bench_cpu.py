@@ -9,16 +9,27 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
+def test_stripe_schedule_covers_the_workload_once():
+    import bench
+    shapes = [(8192, 8192), (2160, 3840), (1080, 1920), (1080, 1920)]
+    sched = bench.stripe_schedule(shapes)
+    assert sum(rows * shapes[i][1] for i, _, rows in sched) == 79_550_464
+    for i, (h, w) in enumerate(shapes):
+        rows = sorted((r0, n) for k, r0, n in sched if k == i)
+        assert rows[0][0] == 0 and sum(n for _, n in rows) == h
+        assert all(a[0] + a[1] == b[0] for a, b in zip(rows, rows[1:]))
+
+
 def test_oracle_pool_counts_samples():
     import bench
     rng = np.random.default_rng(5)
-    plane = rng.integers(0, 256, size=(96, 40), dtype=np.uint8)
-    op = bench.OraclePool(plane, cores=2)
+    planes = [rng.integers(0, 256, size=(96, 40), dtype=np.uint8), rng.integers(0, 256, size=(20, 24), dtype=np.uint8)]
+    op = bench.OraclePool(planes, [False, True], cores=2)
     try:
         assert op.cores == 2
-        # two stripes of 16 rows, then two that wrap around the plane's end
-        assert op.step(0, 16) == 2 * 16 * 40
-        assert op.step(80, 16) == 2 * 16 * 40
+        # the schedule: plane 0 in one 96-row stripe, then plane 1 in one 20-row stripe
+        assert op.step() == 96 * 40 + 20 * 24
+        assert op.step() == 96 * 40 + 20 * 24
     finally:
         op.close()
 
@@ -26,7 +37,7 @@ def test_oracle_pool_counts_samples():
 def test_parallel_baseline_reports_its_cores():
     import bench
     plane = np.full((64, 64), 77, dtype=np.uint8)
-    r = bench.cpu_baseline_parallel(plane, 0.2, rows=16, cores=2)
+    r = bench.cpu_baseline_parallel([plane], [False], 0.2, cores=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
 
 
