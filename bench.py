@@ -540,8 +540,8 @@ def cfg0_line(D, dev, reps=400):
     """The plain method on one 512 x 512 grey image: 8 random 2-D sinusoids
     (periods 4..128 px) scaled to 0..255 plus Gaussian noise sigma 5 (seed 0),
     IJG luminance table at quality 50; compress, reconstruct and SSE in one
-    dct_codec_fused call, and the same work as a one-item batch replayed from
-    its CUDA graph.  Median of `reps` event-timed calls; the 256 KB image
+    dct_codec_fused call, and the same work as a one-item batch (autotuned)
+    replayed from its CUDA graph.  Median of `reps` event-timed calls; the 256 KB image
     stays in the L2 and one call lasts microseconds, so the figure is bound
     by launch latency, not by the roofline."""
     import torch
@@ -562,6 +562,8 @@ def cfg0_line(D, dev, reps=400):
         out["direct_mpix_s"] = img.numel() / (ms * 1e-3) / 1e6
         C, R, S = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE
         D.dct_batch_prepare(plan, D.make_batch_items([img], [50], coeffs=[coef], recons=[rec]), C | R | S, sse=sse)
+        shape, _ = D.dct_autotune(plan)
+        out["graph_shape"] = {"threads_per_cta": shape[0], "ctas_per_sm": shape[1], "lanes_per_block": max(1, shape[3])}
         launch = lambda: D.dct_batch_launch(plan)
         for _ in range(20):
             launch()

@@ -378,9 +378,14 @@ __global__ void __launch_bounds__(256, DCTGB_PAIR_MINB) k_codec_pair(const __gri
         atomicAdd(args.p[threadIdx.x].sse, csse[threadIdx.x]);
 }
 
-// Host launcher of k_codec_pair: one persistent grid of resident CTAs.
+// Host launcher of k_codec_pair: one persistent grid of resident CTAs.  A
+// call with fewer tiles than warps in `num_sms` CTAs of `threads` gets
+// smaller CTAs (down to two warps), so a small plane spreads over more SMs
+// instead of sharing a few SMs' schedulers (a tile takes one warp many
+// microseconds, so that sharing sets the latency of the whole call).
 template <unsigned MODE>
 inline cudaError_t launch_codec_pair(const DirectArgs& a, int num_sms, int threads, cudaStream_t s) {
+    while (threads > 64 && (long long)a.ntiles < (long long)num_sms * (threads / 32)) threads /= 2;
     const size_t smem = pair_codec_smem_bytes(threads);
     cudaError_t e = cudaFuncSetAttribute(k_codec_pair<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

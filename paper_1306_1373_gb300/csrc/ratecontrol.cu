@@ -330,10 +330,14 @@ static dct_status check_frames(dct_plan_t plan, const dct_plane* planes, int k, 
     if (k != 1 && k != 3) return fail(DCT_ERR_INVALID_ARG, "planes_per_frame must be 1 or 3");
     if (nframes < 1 || (long long)nframes * k > plan->desc.max_batch)
         return fail(DCT_ERR_INVALID_ARG, "nframes * planes_per_frame must be 1..max_batch");
+    long long tiles = 0;
     for (long long i = 0; i < (long long)nframes * k; ++i) {
         dct_status st = check_plane(plan, planes[i], "rate-control plane");
         if (st != DCT_OK) return st;
+        const long long nblk = (long long)((planes[i].width + 7) / 8) * ((planes[i].height + 7) / 8);
+        tiles += (nblk + kTileBlocks - 1) / kTileBlocks;
     }
+    if (tiles > (1ll << 30)) return fail(DCT_ERR_INVALID_ARG, "frames too large for one pass (more than 2^30 tiles)");
     for (int f = 0; f < nframes; ++f)
         if (!(target[f] > 0.0f && target[f] < 200.0f)) return fail(DCT_ERR_INVALID_ARG, "targets must be in (0, 200) dB");
     return DCT_OK;
