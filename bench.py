@@ -111,11 +111,10 @@ def make_planes(device):
 
 def algorithmic_ops_per_sample(n):
     """Integer operations per sample of the whole path at N micro-rotations
-    per CORDIC rotation, counted as the survey's measurement plan does: four
-    8-point passes, each 20 butterfly adds + 3 rotations x N x (2 floor
-    shifts + 2 adds) per 8 samples, then quantiser 5, dequantiser with clamp
-    4, level shift / descale / clamp 4 and the SSE term 2 per sample
-    (61 at N = 6).  The kernels issue fewer instructions than this (three-
+    per CORDIC rotation, counted from the method's steps: four 8-point
+    passes, each 20 butterfly adds + 3 rotations x N x (2 floor shifts + 2
+    adds) per 8 samples, then quantiser 5, dequantiser with clamp 4, level
+    shift / descale / clamp 4 and the SSE term 2 per sample (61 at N = 6).  The kernels issue fewer instructions than this (three-
     input adds and shift-left-adds fuse two operations), so the fraction of
     the integer peak it gives counts the method's work, not issue slots."""
     return 4 * (20 + 12 * n) / 8.0 + 15
@@ -1167,7 +1166,8 @@ def main():
     roof = {"bound": "alu", "achieved": achieved_ops, "peak": alu_peak, "unit": "Tops/s (int32)",
             "frac": achieved_ops / alu_peak, "traffic": stored_traffic(kernel, WORKLOAD), "kernel": kernel,
             "ops_per_sample": ops,
-            "ops_source": "4 passes x (20 + 12 N) / 8 + 15 per sample (N = %d): the survey's count" % n_cordic,
+            "ops_source": "4 passes x (20 + 12 N) / 8 + 15 per sample (N = %d): butterflies, CORDIC shifts and adds, "
+                          "quantiser, dequantiser, level shift, descale, SSE" % n_cordic,
             "peak_source": "derived: %d SMs x 4 schedulers x 32 int32 lanes per clock x %.0f MHz (sm_max_mhz)"
                            % (n_sms, sm_mhz_max),
             "peak_measured": {"tops_at_max_clock": meas_peak, "ops_per_clk_sm": meas["ops_per_clk_sm"],
