@@ -1114,10 +1114,9 @@ def main():
         torch.cuda.synchronize()
         link_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
         # The step's result is its metric (the SSE words, from which the PSNR
-        # of Eq. 23 follows on the host): e2e reads back those, as the
-        # contract's "device -> host read of the step's result (loss or
-        # metric)" has it.  with_coefficients is the same pipeline also
-        # copying every int16 code back to the host.
+        # of Eq. 23 follows on the host): e2e reads back those.
+        # with_coefficients is the same pipeline also copying every int16
+        # code back to the host.
         e2e = {"value": replica_throughput(samples, world, metric_ms), "unit": "MPix/s", "ms_per_step": metric_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * len(planes), "steps": e2e_steps,
                "repeats_ms_per_step": metric_rep, "reported": "median of the three repeats",
