@@ -445,8 +445,8 @@ def rate_of_coefficients(D, coefs, shapes):
 def paper_size_sweep(D, dev, reps=50):
     """GPU time of one compress + reconstruct + PSNR pass per image at the
     paper's sizes (1/f^2 noise stand-ins, quality 75), as a one-item batch
-    replayed from its CUDA graph, next to the paper's own times (GTX 480 and
-    i3-2130, context only)."""
+    (autotuned per size) replayed from its CUDA graph, next to the paper's
+    own times (GTX 480 and i3-2130, context only)."""
     import torch
     from synth import powerlaw_image
     out = []
@@ -458,7 +458,8 @@ def paper_size_sweep(D, dev, reps=50):
             rec = torch.empty_like(img)
             sse = torch.zeros(1, dtype=torch.int64, device=dev)
             D.dct_batch_prepare(plan, D.make_batch_items([img], [QUALITY], coeffs=[coef], recons=[rec]), C | R | S,
-                                sse=sse, shape=(256, 8, 32, 0))
+                                sse=sse)
+            shape, _ = D.dct_autotune(plan)
             for _ in range(3):
                 D.dct_batch_launch(plan)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -469,7 +470,7 @@ def paper_size_sweep(D, dev, reps=50):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            out.append({"image": "%s %dx%d" % (name, w, h), "gb300_ms": ms,
+            out.append({"image": "%s %dx%d" % (name, w, h), "gb300_ms": ms, "shape": list(shape),
                         "gb300_mpix_s": w * h / (ms * 1e-3) / 1e6, "paper_gtx480_ms": gpu_ms,
                         "paper_i3_ms": cpu_ms, "psnr_db": D.dct_psnr_from_sse(int(sse[0]), w * h)})
     return out
