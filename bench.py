@@ -121,9 +121,9 @@ def algorithmic_ops_per_sample(n):
 
 
 def int_peak_probe(D, iters=4096, reps=3):
-    """dct_int_peak in its three forms: best of `reps` runs each."""
+    """dct_int_peak in its four forms: best of `reps` runs each."""
     out = {}
-    for kind, name in ((0, "shift_add"), (1, "one_madhi"), (2, "two_madhi")):
+    for kind, name in ((0, "shift_add"), (1, "one_madhi"), (2, "two_madhi"), (3, "float_fma_rd_ru")):
         r = [D.dct_int_peak(kind, iters) for _ in range(reps)]
         out[name] = {"ops_per_clk_sm": max(x[0] for x in r), "tops": max(x[1] for x in r),
                      "ms": min(x[2] for x in r)}
@@ -480,7 +480,8 @@ def direct_api(D, dev, planes, flush, sse_ref, reps=30):
     """The plane calls of the boundary on the benchmark planes, one call for
     the grey plane and one for the 4:2:0 frame per step, L2 flushed between
     steps: dct_codec_fused (coefficients, reconstruction and SSE in one
-    pass) and dct_compress + dct_reconstruct (with SSE)."""
+    pass), dct_compress + dct_reconstruct (with SSE), and dct_compress
+    alone (its SSE words are those of the previous entry)."""
     import torch
     grey, frame = planes[:1], planes[1:]
     samples = sum(int(p.numel()) for p in planes)
@@ -501,8 +502,12 @@ def direct_api(D, dev, planes, flush, sse_ref, reps=30):
                 D.dct_compress(plan, src, QUALITY, coeffs=coef)
                 D.dct_reconstruct(plan, coef, rec, QUALITY, ref_planes=src, sse=sse)
 
+        def compress_only():
+            for plan, src, coef, rec, sse in sets:
+                D.dct_compress(plan, src, QUALITY, coeffs=coef)
+
         stream = torch.cuda.current_stream()
-        for name, fn in (("codec_fused", fused), ("compress_reconstruct", two_calls)):
+        for name, fn in (("codec_fused", fused), ("compress_reconstruct", two_calls), ("compress", compress_only)):
             for _ in range(3):
                 flush.zero_()
                 fn()

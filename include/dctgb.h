@@ -461,11 +461,13 @@ dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, uint32_t op
  * for the roofline of the codec kernels, which are bound by integer
  * instruction issue).  Runs `iters` iterations of 32 CORDIC micro-rotations
  * (a, b) <- (a + (b >> i), b - (a >> i)), i in 2..6, per thread on 8
- * independent chains, over every SM, in one of three instruction forms:
- * kind 0 shift + add for both halves (the form the codec kernels use);
- * kind 1 one half as mad.hi.s32, the other as shift + add; kind 2 both
- * halves as mad.hi.s32.  Counts 4 integer operations (2 floor shifts, 2 adds) per
- * micro-rotation.  Host outputs (any may be NULL): operations per clock per
+ * independent chains, over every SM, in one of four instruction forms:
+ * kind 0 shift + add for both halves (the inverse kernels' form, and the
+ * forward kernels' for i = 1); kind 1 one half as mad.hi.s32, the other as
+ * shift + add; kind 2 both halves as mad.hi.s32; kind 3 both halves as
+ * float32 fused multiply-adds with directed rounding (the forward kernels'
+ * form for i >= 2, exact on their biased operands).  Counts 4 integer
+ * operations (2 floor shifts, 2 adds) per micro-rotation.  Host outputs (any may be NULL): operations per clock per
  * SM (from clock64 spans, independent of the clock the GPU ran at),
  * Tops/s and the kernel time in ms.  Allocates two small device buffers;
  * synchronises `stream`.  iters in 1..2^24. */

@@ -1,7 +1,7 @@
 // Integer issue-rate probe (no counterpart in the paper): the throughput of
 // the codec's dominant operation, the CORDIC micro-rotation
 // (a, b) <- (a + (b >> i), b - (a >> i)) of Sec. 2.5.2's rotation blocks,
-// measured on this GPU in three instruction forms.  The codec is bound by
+// measured on this GPU in four instruction forms.  The codec is bound by
 // integer instruction issue, so this rate (not HBM bandwidth) is the
 // roofline its kernels are held against.
 //
@@ -11,6 +11,10 @@
 //   kind 2  both halves as mad.hi.s32 (the second on ~a, exact:
 //           b - (a >> i) = b + ((~a) >> i) + 1 folded as a constant)
 //                                                  (2 instructions + 1 not)
+//   kind 3  both halves as float32 fused multiply-adds with directed
+//           rounding (the forward kernels' form for micro-rotations
+//           2..N: on biased values in [2^23, 2^24) they round to exactly
+//           a + floor(b / 2^i))                    (2 instructions)
 //
 // Every thread runs 8 independent micro-rotation chains; the grid fills
 // every SM with resident CTAs.  Cycles come from clock64() per CTA, so the
@@ -30,7 +34,12 @@ __device__ __forceinline__ int peak_madhi(int acc, int v) {
 
 template <int KIND, int I>
 __device__ __forceinline__ void peak_step(int& a, int& b) {
-    if constexpr (KIND == 0) {
+    if constexpr (KIND == 3) {
+        constexpr float sc = 1.0f / float(1 << I);
+        const float fa = __int_as_float(a), fb = __int_as_float(b);
+        b = __float_as_int(__fmaf_ru(fa, -sc, fb));
+        a = __float_as_int(__fmaf_rd(fb, sc, fa));
+    } else if constexpr (KIND == 0) {
         const int na = a + (b >> I);
         b = b - (a >> I);
         a = na;
@@ -55,6 +64,10 @@ __global__ void __launch_bounds__(256) k_int_peak(int iters, int* sink, long lon
     for (int k = 0; k < kPeakChains; ++k) {
         a[k] = (int)(threadIdx.x * 2654435761u) ^ (k * 40503);
         b[k] = (int)(blockIdx.x * 97u + k * 1013904223u);
+        if (KIND == 3) {            // floats of magnitude near 2^23 (finite)
+            a[k] = (int)(0x4B000000u + ((unsigned)a[k] & 0xFFFFu));
+            b[k] = (int)(0xCB000000u + ((unsigned)b[k] & 0xFFFFu));
+        }
     }
     __syncthreads();
     const long long t0 = clock64();
@@ -88,13 +101,14 @@ using namespace dctgb;
 
 extern "C" dct_status dct_int_peak(int kind, int iters, double* ops_per_clk_sm_host, double* tops_host,
                                    float* ms_host, dct_stream_t stream) {
-    if (kind < 0 || kind > 2) return fail(DCT_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 3) return fail(DCT_ERR_INVALID_ARG, "kind must be 0, 1, 2 or 3");
     if (iters < 1 || iters > (1 << 24)) return fail(DCT_ERR_INVALID_ARG, "iters must be 1..2^24");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
-    void (*kp)(int, int*, long long*) = kind == 0 ? k_int_peak<0> : (kind == 1 ? k_int_peak<1> : k_int_peak<2>);
+    void (*kp)(int, int*, long long*) =
+        kind == 0 ? k_int_peak<0> : (kind == 1 ? k_int_peak<1> : (kind == 2 ? k_int_peak<2> : k_int_peak<3>));
     const int threads = 256;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, threads, 0);

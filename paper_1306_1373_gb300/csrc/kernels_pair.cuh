@@ -181,7 +181,7 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
 #pragma unroll
                 for (int col = 0; col < 8; ++col) v[j][col] = (sample4(pix, j, col) - 128) * (1 << kP);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) loeffler8_fwd(v[j]);
+            for (int j = 0; j < 4; ++j) loeffler8_fwd<false>(v[j]);
 
             // the samples wait for the SSE in this lane's slot (the two 16-byte
             // halves swap on every fourth lane: no bank conflicts)
@@ -206,7 +206,7 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
 
             // column pass: c[i][u] = Y[u][4h + i]
 #pragma unroll
-            for (int i = 0; i < 4; ++i) loeffler8_fwd(c[i]);
+            for (int i = 0; i < 4; ++i) loeffler8_fwd<false>(c[i]);
 
             // quantiser: high word of Y M + 2^31, with - [Y < 0] at the tie
             // entries (u, v in {0, 4}: i = 0 and u = 0 or 4 in both lanes)

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kRgbThreads, 6) k_compress_rgb(const __grid_co
                 for (int c = 0; c < 8; ++c)
                     x[r][c] = ((int)(((c < 4 ? w.x : w.y) >> (8 * (c & 3))) & 0xFFu) - 128) * (1 << kP);
             }
-            fwd2d(x);
+            fwd2d<false>(x);
             quantize_fwd(x, tabs[luma ? 0 : 1]);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {

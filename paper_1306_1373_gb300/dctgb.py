@@ -491,7 +491,7 @@ def dct_batch_run_noalloc(items, ops, sse=None, stream=None):
 
 def dct_int_peak(kind=1, iters=4096, stream=None):
     """Integer issue-rate probe: (ops per clock per SM, Tops/s, ms) for the
-    CORDIC micro-rotation in instruction form ``kind`` (0, 1 or 2)."""
+    CORDIC micro-rotation in instruction form ``kind`` (0, 1, 2 or 3)."""
     opc, tops, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_float()
     _check(load().dct_int_peak(int(kind), int(iters), ctypes.byref(opc), ctypes.byref(tops), ctypes.byref(ms),
                                _stream_ptr(stream)))
