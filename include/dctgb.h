@@ -336,7 +336,8 @@ dct_status dct_autotune(dct_plan_t plan, dct_launch_shape* best, float* ms_host,
  * quality is clamp(rint(1 + 99 y), 1, 100).  All arrays are device float32
  * owned by the caller. */
 typedef struct {
-    float* params;        /* DCT_MLP_PARAMS: W1[64][80], b1[64], W2[64][64], b2[64], W3[64], b3 */
+    float* params;        /* DCT_MLP_PARAMS: W1[64][80], b1[64], W2[64][64], b2[64], W3[64], b3;
+                             16-byte aligned */
     float* adam_m;        /* DCT_MLP_PARAMS, Adam first moments (training only) */
     float* adam_v;        /* DCT_MLP_PARAMS, Adam second moments (training only) */
     float* feat_mean;     /* DCT_MLP_INPUTS */
@@ -367,7 +368,8 @@ dct_status dct_mlp_forward(const dct_mlp* net, const float* feats, int n, float*
  * predicts. */
 dct_status dct_mlp_labels(const int32_t* quality, int n, float* labels_out, dct_stream_t stream);
 
-/* Bytes of device workspace dct_mlp_loss_grad needs for a minibatch of `batch` rows. */
+/* Bytes of device workspace dct_mlp_loss_grad needs for a minibatch of
+ * `batch` rows (the workspace must be 16-byte aligned). */
 size_t dct_mlp_workspace_bytes(int batch);
 
 /* Mean squared error over the minibatch rows index[0..batch) of (feats,
@@ -384,8 +386,11 @@ dct_status dct_mlp_adam(dct_mlp* net, const float* grad, float lr, float beta1, 
 
 /* One epoch of minibatch training: for each consecutive `batch` rows of
  * order[0..n) (device int32, a permutation chosen by the caller) a
- * loss_grad + adam step.  loss_out: device float[ceil(n / batch)].
- * workspace: dct_mlp_workspace_bytes(batch) + DCT_MLP_PARAMS floats. */
+ * loss_grad + adam step (beta1 0.9, beta2 0.999, eps 1e-8), the Adam update
+ * fused into the gradient kernel with the same arithmetic (two launches per
+ * minibatch).  batch in 1..2^20, lr > 0.  loss_out: device
+ * float[ceil(n / batch)].  workspace: dct_mlp_workspace_bytes(batch) +
+ * DCT_MLP_PARAMS floats. */
 dct_status dct_mlp_train_epoch(dct_mlp* net, const float* feats, const float* labels, const int32_t* order, int n,
                                int batch, float lr, float* loss_out, void* workspace, dct_stream_t stream);
 

@@ -3,7 +3,8 @@
 // (fixed-order) minibatch sums, and Adam.  The network is tiny (9409
 // parameters), so it runs on plain FMA units: one thread per sample for
 // inference, one warp per minibatch row for the training forward and delta
-// pass, one thread per parameter for the gradient sums and the update.
+// pass, one thread per parameter for the gradient sums (in tiles that stage
+// the minibatch in shared memory) and the update.
 #include <cmath>
 #include <cstring>
 
@@ -17,10 +18,13 @@ constexpr int kIn = DCT_MLP_INPUTS, kHid = DCT_MLP_HIDDEN, kParams = DCT_MLP_PAR
 constexpr int oW1 = 0, oB1 = kHid * kIn, oW2 = oB1 + kHid, oB2 = oW2 + kHid * kHid, oW3 = oB2 + kHid,
               oB3 = oW3 + kHid;
 static_assert(oB3 + 1 == kParams, "parameter layout");
+static_assert(oW1 % 4 == 0 && oW2 % 4 == 0 && kIn % 4 == 0 && kHid % 4 == 0, "16-byte weight rows");
 
-// per-sample cache (floats): xn[80] a1[64] h1[64] a2[64] h2[64] y dz da2[64] da1[64]
-constexpr int cXn = 0, cA1 = cXn + kIn, cH1 = cA1 + kHid, cA2 = cH1 + kHid, cH2 = cA2 + kHid, cY = cH2 + kHid,
-              cDz = cY + 1, cDa2 = cDz + 1, cDa1 = cDa2 + kHid, kCache = ((cDa1 + kHid + 3) / 4) * 4;
+// per-sample cache (floats): xn[80] a1[64] h1[64] a2[64] h2[64] da2[64]
+// da1[64] y dz, every vector 16-byte aligned (the row is 468 floats)
+constexpr int cXn = 0, cA1 = cXn + kIn, cH1 = cA1 + kHid, cA2 = cH1 + kHid, cH2 = cA2 + kHid, cDa2 = cH2 + kHid,
+              cDa1 = cDa2 + kHid, cY = cDa1 + kHid, cDz = cY + 1, kCache = ((cDz + 1 + 3) / 4) * 4;
+static_assert(cH1 % 4 == 0 && cH2 % 4 == 0 && cDa2 % 4 == 0 && cDa1 % 4 == 0 && kCache % 4 == 0, "cache alignment");
 
 __device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float a) {
@@ -86,14 +90,55 @@ __global__ void k_mlp_forward(const float* __restrict__ P, const float* __restri
 // forward + output delta + hidden deltas of one minibatch row per warp:
 // lane l owns hidden units l and l + 32 of both layers; every sum runs over
 // its inputs in ascending order as forward_sample's does (the inputs a lane
-// does not hold come by shuffle), so the cache holds the same values.
-__global__ void k_mlp_delta(const float* __restrict__ P, const float* __restrict__ feats,
-                            const float* __restrict__ labels, const int* __restrict__ index,
-                            const float* __restrict__ mean, const float* __restrict__ stdv, int bf16, int batch,
-                            float* __restrict__ cache) {
+// does not hold come by shuffle), so the cache holds the same values.  The
+// CTA first stages W1 and W2 transposed in shared memory with rows padded
+// to 65 floats: the forward sums read W^T[i][lane] and the backward sum
+// reads W2[j][lane] = W2^T[lane][j], both free of bank conflicts (reading
+// W1 straight from global memory touched 32 cache lines per warp access).
+constexpr int kDeltaRows = 8;                  // minibatch rows (warps) per CTA
+constexpr int kTStride = kHid + 1;             // padded row of a transposed weight matrix
+
+__global__ void __launch_bounds__(kDeltaRows * 32)
+k_mlp_delta(const float* __restrict__ P, const float* __restrict__ feats, const float* __restrict__ labels,
+            const int* __restrict__ index, const float* __restrict__ mean, const float* __restrict__ stdv, int bf16,
+            int batch, float* __restrict__ cache) {
+    __shared__ float w1t[kIn * kTStride];       // w1t[i * 65 + j] = W1[j][i]
+    __shared__ float w2t[kHid * kTStride];      // w2t[i * 65 + j] = W2[j][i]
+    {
+        // 16-byte loads along the rows of W1 and W2 (both start 16-byte
+        // aligned), all issued before the first shared-memory store
+        constexpr int n1 = kHid * kIn / 4, n2 = kHid * kHid / 4, nv = n1 + n2;
+        constexpr int per = (nv + kDeltaRows * 32 - 1) / (kDeltaRows * 32);
+        const float4* P4 = reinterpret_cast<const float4*>(P);
+        float4 v[per];
+#pragma unroll
+        for (int u = 0; u < per; ++u) {
+            const int e = threadIdx.x + u * kDeltaRows * 32;
+            if (e < n1) v[u] = P4[oW1 / 4 + e];
+            else if (e < nv) v[u] = P4[oW2 / 4 + e - n1];
+        }
+#pragma unroll
+        for (int u = 0; u < per; ++u) {
+            const int e = threadIdx.x + u * kDeltaRows * 32;
+            if (e < n1) {
+                const int j = (4 * e) / kIn, i = 4 * e - j * kIn;
+                w1t[(i + 0) * kTStride + j] = v[u].x;
+                w1t[(i + 1) * kTStride + j] = v[u].y;
+                w1t[(i + 2) * kTStride + j] = v[u].z;
+                w1t[(i + 3) * kTStride + j] = v[u].w;
+            } else if (e < nv) {
+                const int f = 4 * (e - n1), j = f / kHid, i = f - j * kHid;
+                w2t[(i + 0) * kTStride + j] = v[u].x;
+                w2t[(i + 1) * kTStride + j] = v[u].y;
+                w2t[(i + 2) * kTStride + j] = v[u].z;
+                w2t[(i + 3) * kTStride + j] = v[u].w;
+            }
+        }
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= batch) return;                                   // warp-uniform
+    if (b >= batch) return;                                   // warp-uniform, after the only barrier
     const int s = index[b];
     float* c = cache + (size_t)b * kCache;
     const float* x = feats + (size_t)s * kIn;
@@ -111,7 +156,7 @@ __global__ void k_mlp_delta(const float* __restrict__ P, const float* __restrict
     for (int i = 0; i < kIn; ++i) {
         const float v = __shfl_sync(0xffffffffu, xn[i >> 5], i & 31);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) a1[k] = fmaf(P[oW1 + (lane + 32 * k) * kIn + i], v, a1[k]);
+        for (int k = 0; k < 2; ++k) a1[k] = fmaf(w1t[i * kTStride + lane + 32 * k], v, a1[k]);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -126,7 +171,7 @@ __global__ void k_mlp_delta(const float* __restrict__ P, const float* __restrict
     for (int i = 0; i < kHid; ++i) {
         const float v = __shfl_sync(0xffffffffu, h1[i >> 5], i & 31);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) a2[k] = fmaf(P[oW2 + (lane + 32 * k) * kHid + i], v, a2[k]);
+        for (int k = 0; k < 2; ++k) a2[k] = fmaf(w2t[i * kTStride + lane + 32 * k], v, a2[k]);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -153,68 +198,149 @@ __global__ void k_mlp_delta(const float* __restrict__ P, const float* __restrict
     for (int j = 0; j < kHid; ++j) {
         const float d = __shfl_sync(0xffffffffu, da2[j >> 5], j & 31);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) s2[k] = fmaf(d, P[oW2 + j * kHid + lane + 32 * k], s2[k]);
+        for (int k = 0; k < 2; ++k) s2[k] = fmaf(d, w2t[(lane + 32 * k) * kTStride + j], s2[k]);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) c[cDa1 + lane + 32 * k] = s2[k] * gelu_grad(a1[k]);
 }
 
-// one thread per parameter (plus one for the loss): sums over the minibatch
-// in row order
-__global__ void k_mlp_grad(const float* __restrict__ cache, const float* __restrict__ labels,
-                           const int* __restrict__ index, int batch, float* __restrict__ grad,
-                           float* __restrict__ loss) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p > kParams) return;
-    float g = 0.0f;
-    if (p == kParams) {
-        for (int b = 0; b < batch; ++b) {
-            const float d = cache[(size_t)b * kCache + cY] - labels[index[b]];
-            g = fmaf(d, d, g);
-        }
-        *loss = g / (float)batch;
-        return;
-    }
-    if (p < oB1) {
-        const int j = p / kIn, i = p - j * kIn;
-        for (int b = 0; b < batch; ++b) {
-            const float* c = cache + (size_t)b * kCache;
-            g = fmaf(c[cDa1 + j], c[cXn + i], g);
-        }
-    } else if (p < oW2) {
-        const int j = p - oB1;
-        for (int b = 0; b < batch; ++b) g += cache[(size_t)b * kCache + cDa1 + j];
-    } else if (p < oB2) {
-        const int q = p - oW2, j = q / kHid, i = q - j * kHid;
-        for (int b = 0; b < batch; ++b) {
-            const float* c = cache + (size_t)b * kCache;
-            g = fmaf(c[cDa2 + j], c[cH1 + i], g);
-        }
-    } else if (p < oW3) {
-        const int j = p - oB2;
-        for (int b = 0; b < batch; ++b) g += cache[(size_t)b * kCache + cDa2 + j];
-    } else if (p < oB3) {
-        const int j = p - oW3;
-        for (int b = 0; b < batch; ++b) {
-            const float* c = cache + (size_t)b * kCache;
-            g = fmaf(c[cDz], c[cH2 + j], g);
-        }
-    } else {
-        for (int b = 0; b < batch; ++b) g += cache[(size_t)b * kCache + cDz];
-    }
-    grad[p] = g;
+// Per-parameter minibatch sums, one output per thread, each over the rows
+// in ascending order (deterministic).  CTAs 0..15 own the W1 gradients of
+// four hidden units (320 outputs), CTAs 16..31 the W2 gradients of four
+// units (256), CTA 32 the b1 sums, CTA 33 the b2 sums and CTA 34 the W3 and
+// b3 sums and the loss.  Each CTA stages the cache columns it needs for
+// kGradRows rows at a time in shared memory (contiguous reads), then every
+// thread runs its sum over the staged rows.
+constexpr int kGradUnits = 4;
+constexpr int kGradRows = 128;
+constexpr int kW1Tiles = kHid / kGradUnits, kW2Tiles = kHid / kGradUnits;
+constexpr int kGradCtas = kW1Tiles + kW2Tiles + 3;
+constexpr int kGradThreads = kGradUnits * kIn;               // the widest tile
+static_assert(kHid % kGradUnits == 0 && kGradThreads >= kHid + 2, "gradient tiling");
+
+// Adam step for one parameter (k_adam and the fused gradient kernel)
+struct AdamArgs {
+    float* P;
+    float* m;
+    float* v;
+    float lr, b1, b2, eps, c1, c2;
+};
+
+__device__ __forceinline__ void adam_update(const AdamArgs& a, int p, float gi) {
+    const float mi = a.b1 * a.m[p] + (1.0f - a.b1) * gi;
+    const float vi = a.b2 * a.v[p] + (1.0f - a.b2) * gi * gi;
+    a.m[p] = mi;
+    a.v[p] = vi;
+    a.P[p] -= a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
 }
 
-__global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2) {
+// ADAM: also apply the Adam step to each parameter as soon as its sum is
+// final (each parameter belongs to one thread; nothing in this kernel reads
+// the parameters), saving the separate update launch of a training step.
+template <bool ADAM>
+__global__ void __launch_bounds__(kGradThreads)
+k_mlp_grad(const float* __restrict__ cache, const float* __restrict__ labels, const int* __restrict__ index,
+           int batch, float* __restrict__ grad, float* __restrict__ loss, AdamArgs adam) {
+    __shared__ __align__(16) float sm[kGradRows * (kGradUnits + kIn)];
+    const int t = threadIdx.x;
+    const int blk = blockIdx.x;
+    // the staged row: `ncol` floats (a multiple of 4) = na float4 from cache
+    // column ca, then nb float4 from column cb; the last CTA's rows end with
+    // (dz, y - label, 0, 0)
+    int ncol, ca, na, cb, nb;
+    const bool last = blk == kW1Tiles + kW2Tiles + 2;
+    if (blk < kW1Tiles) {
+        ca = cDa1 + kGradUnits * blk; na = kGradUnits / 4; cb = cXn; nb = kIn / 4;
+    } else if (blk < kW1Tiles + kW2Tiles) {
+        ca = cDa2 + kGradUnits * (blk - kW1Tiles); na = kGradUnits / 4; cb = cH1; nb = kHid / 4;
+    } else if (blk == kW1Tiles + kW2Tiles) {
+        ca = cDa1; na = kHid / 4; cb = 0; nb = 0;
+    } else if (blk == kW1Tiles + kW2Tiles + 1) {
+        ca = cDa2; na = kHid / 4; cb = 0; nb = 0;
+    } else {
+        ca = cH2; na = kHid / 4; cb = 0; nb = 0;
+    }
+    const int nv = na + nb + (last ? 1 : 0);
+    ncol = 4 * nv;
+    float4* sm4 = reinterpret_cast<float4*>(sm);
+    const float4* cache4 = reinterpret_cast<const float4*>(cache);
+    float g = 0.0f;
+    for (int r0 = 0; r0 < batch; r0 += kGradRows) {
+        const int rows = min(kGradRows, batch - r0);
+        const int total = rows * nv;
+        __syncthreads();
+        // 16-byte loads, eight in flight per thread before the stores
+        for (int e0 = t; e0 < total; e0 += 8 * kGradThreads) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kGradThreads;
+                if (e < total) {
+                    const int r = e / nv, k = e - r * nv;
+                    const size_t row4 = (size_t)(r0 + r) * (kCache / 4);
+                    if (k < na) {
+                        v[u] = cache4[row4 + ca / 4 + k];
+                    } else if (k < na + nb) {
+                        v[u] = cache4[row4 + cb / 4 + k - na];
+                    } else {
+                        const float* row = cache + (size_t)(r0 + r) * kCache;
+                        v[u] = make_float4(row[cDz], row[cY] - labels[index[r0 + r]], 0.0f, 0.0f);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * kGradThreads;
+                if (e < total) sm4[e] = v[u];
+            }
+        }
+        __syncthreads();
+        if (blk < kW1Tiles + kW2Tiles) {
+            const int nin = blk < kW1Tiles ? kIn : kHid;
+            if (t < kGradUnits * nin) {
+                const int u = t / nin, i = t - u * nin;
+                for (int r = 0; r < rows; ++r) g = fmaf(sm[r * ncol + u], sm[r * ncol + kGradUnits + i], g);
+            }
+        } else if (blk < kW1Tiles + kW2Tiles + 2) {
+            if (t < kHid)
+                for (int r = 0; r < rows; ++r) g += sm[r * ncol + t];
+        } else if (t < kHid) {                           // W3
+            for (int r = 0; r < rows; ++r) g = fmaf(sm[r * ncol + kHid], sm[r * ncol + t], g);
+        } else if (t == kHid) {                          // b3
+            for (int r = 0; r < rows; ++r) g += sm[r * ncol + kHid];
+        } else if (t == kHid + 1) {                      // loss
+            for (int r = 0; r < rows; ++r) {
+                const float d = sm[r * ncol + kHid + 1];
+                g = fmaf(d, d, g);
+            }
+        }
+    }
+    int p = -1;
+    if (blk < kW1Tiles) {
+        if (t < kGradUnits * kIn) p = oW1 + (kGradUnits * blk) * kIn + t;
+    } else if (blk < kW1Tiles + kW2Tiles) {
+        if (t < kGradUnits * kHid) p = oW2 + (kGradUnits * (blk - kW1Tiles)) * kHid + t;
+    } else if (blk == kW1Tiles + kW2Tiles) {
+        if (t < kHid) p = oB1 + t;
+    } else if (blk == kW1Tiles + kW2Tiles + 1) {
+        if (t < kHid) p = oB2 + t;
+    } else if (t < kHid) {
+        p = oW3 + t;
+    } else if (t == kHid) {
+        p = oB3;
+    } else if (t == kHid + 1) {
+        *loss = g / (float)batch;
+    }
+    if (p >= 0) {
+        grad[p] = g;
+        if (ADAM) adam_update(adam, p, g);
+    }
+}
+
+__global__ void k_adam(AdamArgs a, const float* __restrict__ g) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= kParams) return;
-    const float gi = g[p];
-    const float mi = b1 * m[p] + (1.0f - b1) * gi;
-    const float vi = b2 * v[p] + (1.0f - b2) * gi * gi;
-    m[p] = mi;
-    v[p] = vi;
-    P[p] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    adam_update(a, p, g[p]);
 }
 
 // training target of a quality label: (Q - 1) / 99 (IEEE division, as the
@@ -224,23 +350,41 @@ __global__ void k_quality_labels(const int32_t* __restrict__ q, int n, float* __
     if (i < n) out[i] = (float)(q[i] - 1) / 99.0f;
 }
 
-// mean and standard deviation of every feature (one thread per feature, in
-// row order, float64); a standard deviation below 1e-6 becomes 1
-__global__ void k_feat_norm(const float* __restrict__ feats, int n, float* __restrict__ mean,
-                            float* __restrict__ stdv) {
-    const int i = threadIdx.x;
-    if (i >= kIn) return;
+// mean and standard deviation of every feature (float64): one CTA per
+// feature, each thread summing a fixed stride of rows, the partial sums
+// combined in a fixed tree (deterministic); a standard deviation below 1e-6
+// becomes 1
+constexpr int kNormThreads = 256;
+
+__device__ double cta_sum_fixed(double v, double* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kNormThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kNormThreads)
+k_feat_norm(const float* __restrict__ feats, int n, float* __restrict__ mean, float* __restrict__ stdv) {
+    __shared__ double red[kNormThreads];
+    const int i = blockIdx.x;
     double s = 0.0;
-    for (int r = 0; r < n; ++r) s += (double)feats[(size_t)r * kIn + i];
-    const double mu = s / n;
+    for (int r = threadIdx.x; r < n; r += kNormThreads) s += (double)feats[(size_t)r * kIn + i];
+    const double mu = cta_sum_fixed(s, red) / n;
     double v = 0.0;
-    for (int r = 0; r < n; ++r) {
+    for (int r = threadIdx.x; r < n; r += kNormThreads) {
         const double d = (double)feats[(size_t)r * kIn + i] - mu;
         v += d * d;
     }
-    const double sd = sqrt(v / n);
-    mean[i] = (float)mu;
-    stdv[i] = sd < 1e-6 ? 1.0f : (float)sd;
+    const double sd = sqrt(cta_sum_fixed(v, red) / n);
+    if (threadIdx.x == 0) {
+        mean[i] = (float)mu;
+        stdv[i] = sd < 1e-6 ? 1.0f : (float)sd;
+    }
 }
 
 // the 80 features of one frame from its statistics words (float64 arithmetic)
@@ -284,11 +428,38 @@ cudaError_t launch_mlp_forward(const dct_mlp* net, const float* feats, int n, fl
     return cudaGetLastError();
 }
 
+static bool adam_params_ok(float lr, float beta1, float beta2, float eps) {
+    return lr > 0.f && beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f;
+}
+
+// advances the network's step count and returns the Adam arguments of that
+// step (bias corrections computed on the host in float64)
+static AdamArgs next_adam_step(dct_mlp* net, float lr, float beta1, float beta2, float eps) {
+    net->step += 1;
+    const double c1 = 1.0 / (1.0 - std::pow((double)beta1, net->step));
+    const double c2 = 1.0 / (1.0 - std::pow((double)beta2, net->step));
+    return AdamArgs{net->params, net->adam_m, net->adam_v, lr, beta1, beta2, eps, (float)c1, (float)c2};
+}
+
+// one minibatch: forward and deltas (one warp per row, 8 rows per CTA,
+// weights staged once per CTA), then one CTA per gradient tile
+template <bool ADAM>
+static cudaError_t launch_train_step(const dct_mlp* net, const float* feats, const float* labels, const int* index,
+                                     int batch, float* grad, float* loss, void* workspace, AdamArgs adam,
+                                     cudaStream_t s) {
+    float* cache = static_cast<float*>(workspace);
+    k_mlp_delta<<<(batch + kDeltaRows - 1) / kDeltaRows, kDeltaRows * 32, 0, s>>>(
+        net->params, feats, labels, index, net->feat_mean, net->feat_std, net->act_bf16, batch, cache);
+    k_mlp_grad<ADAM><<<kGradCtas, kGradThreads, 0, s>>>(cache, labels, index, batch, grad, loss, adam);
+    return cudaGetLastError();
+}
+
 static dct_status check_net(const dct_mlp* net, bool train) {
     if (!net || !net->params || !net->feat_mean || !net->feat_std)
         return fail(DCT_ERR_INVALID_ARG, "network pointers are null");
     if (train && (!net->adam_m || !net->adam_v)) return fail(DCT_ERR_INVALID_ARG, "Adam state pointers are null");
     if (net->act_bf16 != 0 && net->act_bf16 != 1) return fail(DCT_ERR_INVALID_ARG, "act_bf16 must be 0 or 1");
+    if (((uintptr_t)net->params) & 15u) return fail(DCT_ERR_INVALID_ARG, "params must be 16-byte aligned");
     return DCT_OK;
 }
 
@@ -311,7 +482,7 @@ dct_status dct_mlp_set_norm(dct_mlp* net, const float* feats, int n, dct_stream_
     dct_status st = check_net(net, false);
     if (st != DCT_OK) return st;
     if (!feats || n < 1) return fail(DCT_ERR_INVALID_ARG, "feats null or n < 1");
-    k_feat_norm<<<1, 128, 0, (cudaStream_t)stream>>>(feats, n, net->feat_mean, net->feat_std);
+    k_feat_norm<<<kIn, kNormThreads, 0, (cudaStream_t)stream>>>(feats, n, net->feat_mean, net->feat_std);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "norm launch");
 }
@@ -345,14 +516,9 @@ dct_status dct_mlp_loss_grad(const dct_mlp* net, const float* feats, const float
     if (!feats || !labels || !index || !grad_out || !loss_out || !workspace)
         return fail(DCT_ERR_INVALID_ARG, "null pointer");
     if (batch < 1 || batch > (1 << 20)) return fail(DCT_ERR_INVALID_ARG, "batch must be 1..2^20");
-    cudaStream_t s = (cudaStream_t)stream;
-    float* cache = static_cast<float*>(workspace);
-    // one warp per row (4 rows per CTA); 64-thread CTAs for the per-parameter
-    // sums so that they spread over every SM
-    k_mlp_delta<<<(batch + 3) / 4, 128, 0, s>>>(net->params, feats, labels, index, net->feat_mean, net->feat_std,
-                                                net->act_bf16, batch, cache);
-    k_mlp_grad<<<(kParams + 1 + 63) / 64, 64, 0, s>>>(cache, labels, index, batch, grad_out, loss_out);
-    cudaError_t e = cudaGetLastError();
+    if (((uintptr_t)workspace) & 15u) return fail(DCT_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    cudaError_t e = launch_train_step<false>(net, feats, labels, index, batch, grad_out, loss_out, workspace,
+                                             AdamArgs{}, (cudaStream_t)stream);
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "gradient launch");
 }
 
@@ -361,13 +527,8 @@ dct_status dct_mlp_adam(dct_mlp* net, const float* grad, float lr, float beta1, 
     dct_status st = check_net(net, true);
     if (st != DCT_OK) return st;
     if (!grad) return fail(DCT_ERR_INVALID_ARG, "null grad");
-    if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
-        return fail(DCT_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
-    net->step += 1;
-    const double c1 = 1.0 / (1.0 - std::pow((double)beta1, net->step));
-    const double c2 = 1.0 / (1.0 - std::pow((double)beta2, net->step));
-    k_adam<<<(kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(net->params, net->adam_m, net->adam_v, grad, lr,
-                                                                    beta1, beta2, eps, (float)c1, (float)c2);
+    if (!adam_params_ok(lr, beta1, beta2, eps)) return fail(DCT_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+    k_adam<<<(kParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(next_adam_step(net, lr, beta1, beta2, eps), grad);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DCT_OK : cuda_fail(e, "adam launch");
 }
@@ -377,14 +538,17 @@ dct_status dct_mlp_train_epoch(dct_mlp* net, const float* feats, const float* la
     dct_status st = check_net(net, true);
     if (st != DCT_OK) return st;
     if (!feats || !labels || !order || !loss_out || !workspace) return fail(DCT_ERR_INVALID_ARG, "null pointer");
-    if (n < 1 || batch < 1) return fail(DCT_ERR_INVALID_ARG, "n and batch must be >= 1");
+    if (n < 1 || batch < 1 || batch > (1 << 20)) return fail(DCT_ERR_INVALID_ARG, "n >= 1 and batch in 1..2^20");
+    if (!adam_params_ok(lr, 0.9f, 0.999f, 1e-8f)) return fail(DCT_ERR_INVALID_ARG, "learning rate must be > 0");
+    if (((uintptr_t)workspace) & 15u) return fail(DCT_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
     float* grad = reinterpret_cast<float*>(static_cast<char*>(workspace) + dct_mlp_workspace_bytes(batch));
+    // per minibatch: the delta kernel, then the gradient sums with the Adam
+    // step fused (same arithmetic as dct_mlp_loss_grad + dct_mlp_adam)
     for (int b0 = 0, k = 0; b0 < n; b0 += batch, ++k) {
         const int cnt = n - b0 < batch ? n - b0 : batch;
-        st = dct_mlp_loss_grad(net, feats, labels, order + b0, cnt, grad, loss_out + k, workspace, stream);
-        if (st != DCT_OK) return st;
-        st = dct_mlp_adam(net, grad, lr, 0.9f, 0.999f, 1e-8f, stream);
-        if (st != DCT_OK) return st;
+        cudaError_t e = launch_train_step<true>(net, feats, labels, order + b0, cnt, grad, loss_out + k, workspace,
+                                                next_adam_step(net, lr, 0.9f, 0.999f, 1e-8f), (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "training step launch");
     }
     return DCT_OK;
 }
