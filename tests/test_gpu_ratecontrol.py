@@ -87,6 +87,29 @@ def test_forward_and_gradient_match_oracle(D, bf16):
     assert np.max(np.abs(g - g_or)) <= (2e-2 if bf16 else 1e-4) * scale
 
 
+@pytest.mark.parametrize("b", [1, 127, 128, 300])
+def test_gradient_over_staged_row_chunks_matches_oracle(D, b):
+    """The gradient kernel stages 128 minibatch rows at a time: minibatches
+    of 1, 127, 128 and 300 rows (two full chunks and a ragged one) against
+    the oracle's float64 gradient, fp32 activations."""
+    rng = np.random.default_rng(11 + b)
+    n = 400
+    x = (rng.normal(size=(n, 80)) * 2 - 1).astype(np.float32)
+    t = rng.uniform(0, 1, n).astype(np.float32)
+    net = D.Mlp(mlp.init_params(7) + rng.normal(0, 0.02, mlp.N_PARAMS), act_bf16=False)
+    X = torch.from_numpy(x).cuda()
+    net.set_norm(X)
+    mean32 = net.mean.cpu().numpy().astype(np.float64)
+    std32 = net.std.cpu().numpy().astype(np.float64)
+    p32 = net.params.cpu().numpy().astype(np.float64)
+    sel = rng.permutation(n)[:b].astype(np.int32)
+    loss, grad = net.loss_grad(X, torch.from_numpy(t).cuda(), torch.from_numpy(sel).cuda())
+    l_or, g_or = mlp.loss_and_grad(p32, x[sel].astype(np.float64), t[sel], mean32, std32, "fp32")
+    assert abs(float(loss) - l_or) <= 1e-5 * max(l_or, 1e-3)
+    g = grad.cpu().numpy()
+    assert np.max(np.abs(g - g_or)) <= 1e-4 * np.max(np.abs(g_or))
+
+
 def test_adam_and_training_epochs_match_oracle(D):
     rng = np.random.default_rng(4)
     n = 200

@@ -206,3 +206,35 @@ def test_fault_injection_hook_is_host_only(lib):
     with pytest.raises(D.DctError) as ei:
         D.dct_debug_fail_alloc(-1)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("case", ["params_align", "workspace_align", "batch_zero", "batch_big", "lr", "null"])
+def test_training_calls_refuse_on_the_host(lib, case):
+    """dct_mlp_loss_grad / dct_mlp_train_epoch check their arguments before
+    any launch: misaligned parameters or workspace (the kernels use 16-byte
+    loads), minibatch sizes outside 1..2^20, a learning rate <= 0, null
+    pointers.  The pointers are fake and never dereferenced."""
+    import ctypes
+    from paper_1306_1373_gb300 import dctgb as D
+    net = D.dct_mlp(0x10000, 0x20000, 0x30000, 0x40000, 0x50000, 0, 1)
+    ws, batch, lr, feats = 0x60000, 256, 1e-3, 0x70000
+    if case == "params_align":
+        net.params = 0x10004
+    elif case == "workspace_align":
+        ws = 0x60008
+    elif case == "batch_zero":
+        batch = 0
+    elif case == "batch_big":
+        batch = (1 << 20) + 1
+    elif case == "lr":
+        lr = 0.0
+    elif case == "null":
+        feats = 0
+    P = ctypes.c_void_p
+    st = lib.dct_mlp_train_epoch(ctypes.byref(net), P(feats), P(0x80000), P(0x90000), 1000, batch,
+                                 ctypes.c_float(lr), P(0xA0000), P(ws), None)
+    assert st == 1, (case, st, lib.dct_last_error())
+    if case != "lr":
+        st = lib.dct_mlp_loss_grad(ctypes.byref(net), P(feats), P(0x80000), P(0x90000), batch, P(0xB0000),
+                                   P(0xA0000), P(ws), None)
+        assert st == 1, (case, st, lib.dct_last_error())
