@@ -231,6 +231,10 @@ static KernelPtr pair_kernel_c(unsigned mode) {
         case kLoadPix | kStoreCoef: return k_batch_pair<kLoadPix | kStoreCoef, C>;
         case kLoadCoef | kInverse | kStoreRecon: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon, C>;
         case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kSse, C>;
+        case kLoadCoef | kInverse | kStoreRecon | kOwnCodes:
+            return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kOwnCodes, C>;
+        case kLoadCoef | kInverse | kStoreRecon | kSse | kOwnCodes:
+            return k_batch_pair<kLoadCoef | kInverse | kStoreRecon | kSse | kOwnCodes, C>;
         case kLoadPix | kInverse | kSse: return k_batch_pair<kLoadPix | kInverse | kSse, C>;
         case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreCoef, C>;
         case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch_pair<kLoadPix | kInverse | kSse | kStoreRecon, C>;
@@ -267,6 +271,9 @@ static KernelPtr one_lane_kernel(unsigned mode) {
         case kLoadPix | kStats: return k_batch<kLoadPix | kStats | kStatsPrivate>;
         case kLoadCoef | kInverse | kStoreRecon: return k_batch<kLoadCoef | kInverse | kStoreRecon>;
         case kLoadCoef | kInverse | kStoreRecon | kSse: return k_batch<kLoadCoef | kInverse | kStoreRecon | kSse>;
+        case kLoadCoef | kInverse | kStoreRecon | kOwnCodes: return k_batch<kLoadCoef | kInverse | kStoreRecon | kOwnCodes>;
+        case kLoadCoef | kInverse | kStoreRecon | kSse | kOwnCodes:
+            return k_batch<kLoadCoef | kInverse | kStoreRecon | kSse | kOwnCodes>;
         case kLoadPix | kInverse | kSse: return k_batch<kLoadPix | kInverse | kSse>;
         case kLoadPix | kInverse | kSse | kStoreCoef: return k_batch<kLoadPix | kInverse | kSse | kStoreCoef>;
         case kLoadPix | kInverse | kSse | kStoreRecon: return k_batch<kLoadPix | kInverse | kSse | kStoreRecon>;
@@ -544,8 +551,10 @@ dct_status dct_batch_prepare(dct_plan_t plan, const dct_batch_item* items, int n
     b->ntiles = cursor;
     b->ntabs = ntabs;
     if (two) {
+        // the inverse kernel reads back the codes the forward kernel of the
+        // same graph has just written
         b->modes[0] = kLoadPix | kStoreCoef;
-        b->modes[1] = mode;
+        b->modes[1] = mode | kOwnCodes;
         b->nkernels = 2;
     } else {
         b->modes[0] = mode;

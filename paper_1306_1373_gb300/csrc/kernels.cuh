@@ -70,7 +70,9 @@ enum : unsigned {
     kStoreRecon = 16u, // write the reconstruction
     kSse = 32u,        // accumulate the SSE
     kStats = 64u,      // accumulate band-energy and pixel statistics
-    kStatsPrivate = 128u // the statistics sink is this warp's own: plain adds, no atomics
+    kStatsPrivate = 128u, // the statistics sink is this warp's own: plain adds, no atomics
+    kOwnCodes = 256u      // the coefficients read back are this library's own codes, written by the
+                          // forward kernel of the same graph: the dequantiser clamp never acts
 };
 
 // Forward micro-rotations 2..N in the float form (cordic_loeffler.cuh) for
@@ -461,14 +463,15 @@ __device__ __forceinline__ unsigned process_tile(const PlaneArg& P, const QuantS
 
     if (MODE & kInverse) {
         // Dequantiser G = clamp(q Q, -4096, 4096) W.  When q comes from this
-        // kernel's own quantiser, |q Q| <= |X| + Q/2 + 1 < 1200 (the Cordic
+        // library's quantiser (this kernel's, or the forward kernel's of the
+        // same two-pass graph), |q Q| <= |X| + Q/2 + 1 < 1200 (the Cordic
         // coefficient |X| is within 14 of an orthonormal DCT value, itself at
         // most 1024), so the clamp never acts and G = q (Q W) exactly.
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
-                if (MODE & kLoadPix) {
+                if (MODE & (kLoadPix | kOwnCodes)) {
                     x[u][v] = x[u][v] * T.QW[u * 8 + v];
                 } else {
                     int t = x[u][v] * T.Q[u * 8 + v];

@@ -264,15 +264,28 @@ __device__ __forceinline__ unsigned process_tile_pair(const PlaneArg& P, const Q
 #pragma unroll
                 for (int u = 0; u < 8; ++u) c[0][u] = c[1][u] = c[2][u] = c[3][u] = 0;
             }
-            // dequantiser G = clamp(q Q, -4096, 4096) W for arbitrary codes
+            if constexpr ((MODE & kOwnCodes) != 0) {
+                // this library's own codes (two-pass graph): G = q (Q W), the
+                // clamp never acts (|q Q| < 1200)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int4 q4 = *reinterpret_cast<const int4*>(Qh + u * 8);
-                const int4 w4 = *reinterpret_cast<const int4*>(Wh + u * 8);
-                c[0][u] = max(-kDequantClamp, min(kDequantClamp, c[0][u] * q4.x)) * w4.x;
-                c[1][u] = max(-kDequantClamp, min(kDequantClamp, c[1][u] * q4.y)) * w4.y;
-                c[2][u] = max(-kDequantClamp, min(kDequantClamp, c[2][u] * q4.z)) * w4.z;
-                c[3][u] = max(-kDequantClamp, min(kDequantClamp, c[3][u] * q4.w)) * w4.w;
+                for (int u = 0; u < 8; ++u) {
+                    const int4 qw = *reinterpret_cast<const int4*>(QWh + u * 8);
+                    c[0][u] *= qw.x;
+                    c[1][u] *= qw.y;
+                    c[2][u] *= qw.z;
+                    c[3][u] *= qw.w;
+                }
+            } else {
+                // dequantiser G = clamp(q Q, -4096, 4096) W for arbitrary codes
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int4 q4 = *reinterpret_cast<const int4*>(Qh + u * 8);
+                    const int4 w4 = *reinterpret_cast<const int4*>(Wh + u * 8);
+                    c[0][u] = max(-kDequantClamp, min(kDequantClamp, c[0][u] * q4.x)) * w4.x;
+                    c[1][u] = max(-kDequantClamp, min(kDequantClamp, c[1][u] * q4.y)) * w4.y;
+                    c[2][u] = max(-kDequantClamp, min(kDequantClamp, c[2][u] * q4.z)) * w4.z;
+                    c[3][u] = max(-kDequantClamp, min(kDequantClamp, c[3][u] * q4.w)) * w4.w;
+                }
             }
         }
         if constexpr ((MODE & kInverse) != 0) {

@@ -68,7 +68,7 @@ extern "C" dct_status dct_batch_run_noalloc(const dct_batch_item* items, int n, 
     if (two && !(comp && rec)) return fail(DCT_ERR_INVALID_ARG, "DCT_OP_TWO_PASS needs COMPRESS|RECONSTRUCT");
 
     unsigned mode;
-    if (two) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
+    if (two) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u) | kOwnCodes;   // reads its own codes
     else if (comp && !rec && !sse) mode = kLoadPix | kStoreCoef;
     else if (rec && !comp) mode = kLoadCoef | kInverse | kStoreRecon | (sse ? kSse : 0u);
     else mode = kLoadPix | kInverse | (sse ? kSse : 0u) | (comp ? kStoreCoef : 0u) | (rec ? kStoreRecon : 0u);
