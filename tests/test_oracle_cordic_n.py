@@ -24,8 +24,9 @@ def test_word_widths_at_every_n(n):
     i_col, i_row = interval.inverse_bounds(n=n)
     i_col2, i_row2 = interval.inverse_bounds(dc_offset=(1 << (spec.R + 2)) + (128 << (spec.R + 3)), n=n)
     assert max(f_row, f_col, i_col, i_row, i_col2, i_row2) < 2 ** 31
-    # the tie-free quantiser argument needs |Y| < 2^20, and the fused
-    # kernels' dequantiser q * (Q W) needs |q Q| within the 4096 clamp
+    # the tie-free quantiser argument needs |Y| < 2^20, and the clamp-free
+    # dequantiser q * (Q W) of the fused kernels and of the two-pass inverse
+    # (which reads back its own graph's codes) needs |q Q| within the 4096 clamp
     assert f_col < 2 ** 20
     bits, _ = interval.worst_case_product_bits(f_col, n=n)
     assert bits <= 63
