@@ -3,8 +3,10 @@ nodes: blocks holding the sign pattern of every 2-D cosine basis (0 and
 255 on the two signs, and the reverse), which drive the transform's
 outputs towards their interval bounds, plus checkerboards, edges and
 constant blocks, through every forward-only entry (direct compress, the
-batched forward pass in both tile layouts, the statistics pass) at N = 4,
-5 and 6, against the oracle bit for bit (Sec. 2.5.2)."""
+batched forward pass in both tile layouts, the statistics pass) and the
+two-pass graph (whose inverse kernel reads its own codes without the
+dequantiser clamp) at N = 4, 5 and 6, against the oracle bit for bit
+(Sec. 2.5.2)."""
 import numpy as np
 import pytest
 import torch
@@ -67,3 +69,32 @@ def test_forward_entries_at_extreme_nodes(D, n, quality):
     y = codec.forward_coefficients(codec.plane_to_blocks(img).reshape(-1, 8, 8), n)
     band = ((np.abs(y) >> 5) ** 2).sum(axis=0).reshape(-1)
     assert np.array_equal(st.cpu().numpy()[:64], band)
+
+
+@pytest.mark.parametrize("n", NS)
+@pytest.mark.parametrize("quality", [1, 50, 100])
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_two_pass_inverse_on_own_codes_at_extremes(D, n, quality, lanes):
+    """The two-pass graph's inverse kernel dequantises the codes its forward
+    kernel wrote without the clamp (|q Q| stays far inside 4096); at the
+    extreme blocks and the coarsest and finest tables its reconstruction and
+    SSE equal the oracle's clamped definition."""
+    from oracle import psnr
+    img = extreme_image()
+    Q = ijg.luma_table(quality)
+    c_or = codec.compress_plane(img, Q, n)
+    r_or = codec.reconstruct_plane(c_or, Q, *img.shape, n=n)
+    t = torch.from_numpy(img).cuda()
+    C, R, S, T = D.DCT_OP_COMPRESS, D.DCT_OP_RECONSTRUCT, D.DCT_OP_SSE, D.DCT_OP_TWO_PASS
+    with D.cordic_variant(n):
+        with D.Plan(img.shape[1], img.shape[0], max_batch=2) as plan:
+            coef = torch.zeros(c_or.size, dtype=torch.int16, device="cuda")
+            rec = torch.zeros_like(t)
+            sse = torch.zeros(1, dtype=torch.int64, device="cuda")
+            D.dct_batch_prepare(plan, D.make_batch_items([t], [quality], coeffs=[coef], recons=[rec]), C | R | S | T,
+                                sse=sse, shape=(128, 4, 32, lanes))
+            D.dct_batch_launch(plan)
+            torch.cuda.synchronize()
+    assert np.array_equal(coef.cpu().numpy(), c_or.reshape(-1))
+    assert np.array_equal(rec.cpu().numpy(), r_or)
+    assert int(sse[0]) == psnr.sse(img, r_or)
